@@ -1,0 +1,71 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/heat_oracle.c`` (a dropped
+term, a wrong sign or index, a transposed operand, a wrong factor), compiles it
+on the CPU and runs the pin suite against it: the suite must fail.  The
+unmodified copy must pass.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "heat_oracle.c")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+MUTANTS = {
+    "drop_radial_metric": ("o->Arm[c] = o->rf[i] * lf / (ri * hb * o->h[i]);",
+                           "o->Arm[c] = lf / (hb * o->h[i]);"),
+    "wrong_h_index": ("o->Arm[c] = o->rf[i] * lf / (ri * hb * o->h[i]);",
+                      "o->Arm[c] = o->rf[i] * lf / (ri * hb * o->h[i + 1]);"),
+    "hbar_not_averaged": ("o->hbar[i] = 0.5 * (o->h[i] + o->h[i + 1]);", "o->hbar[i] = o->h[i + 1];"),
+    "axis_face_not_zero": ("o->rf[0] = o->r_lo;", "o->rf[0] = 0.5 * o->rc[0];"),
+    "harmonic_weights_swapped": ("return (da + db) / (da / ka + db / kb);",
+                                 "return (da + db) / (db / ka + da / kb);"),
+    "dirichlet_factor_dropped": ("o->Dzh[c] = 2.0 * lam / (eb * o->eta[Nz]);",
+                                 "o->Dzh[c] = lam / (eb * o->eta[Nz]);"),
+    "explicit_z_sign": ("if (o->Azp[c] != 0.0) s += o->Azp[c] * (T[IDX(o, i, j + 1)] - t);",
+                        "if (o->Azp[c] != 0.0) s += o->Azp[c] * (t - T[IDX(o, i, j + 1)]);"),
+    "transposed_offdiagonals": ("                a[i] = -o->Arm[c];\n                cc[i] = -o->Arp[c];",
+                                "                a[i] = -o->Arp[c];\n                cc[i] = -o->Arm[c];"),
+    "thomas_pivot": ("dw[i] = (d[i] - a[i] * dw[i - 1]) / m;", "dw[i] = (d[i] - a[i] * dw[i - 1]) / b[i];"),
+    "full_tau_in_half_step": ("const double half = 0.5 * tau;", "const double half = tau;"),
+    "source_dropped_in_half_step_2": (
+        "d[j] = w * Tb[c] + lambda_r(o, Tb, i, j) + xs + o->Dzl[c] * o->Tbc[2] + o->Dzh[c] * o->Tbc[3];",
+        "d[j] = w * Tb[c] + lambda_r(o, Tb, i, j) + o->Dzl[c] * o->Tbc[2] + o->Dzh[c] * o->Tbc[3];"),
+    "energy_weight_cell_width": ("double wgt = o->rc[i] * o->hbar[i] * o->etabar[j];",
+                                 "double wgt = o->rc[i] * o->dr[i] * o->etabar[j];"),
+}
+
+
+def _build(tmp_path, name, src_text):
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"lib_{name}.so"
+    c.write_text(src_text)
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", str(c), "-o", str(so), "-lm"])
+    return str(so)
+
+
+def _run_pins(so):
+    env = dict(os.environ, HEAT_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    return r.returncode, r.stdout[-2000:]
+
+
+def test_unmodified_copy_passes(tmp_path):
+    so = _build(tmp_path, "orig", open(SRC).read())
+    rc, out = _run_pins(so)
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    so = _build(tmp_path, name, text.replace(old, new))
+    rc, out = _run_pins(so)
+    assert rc != 0, f"pins did not catch {name}:\n{out}"
