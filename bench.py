@@ -1,0 +1,311 @@
+"""Benchmark of the ADI heat step on the 2048 x 4096 five-region cell.
+
+Workload: the layered cryogenic cell of the paper's Fig. "object" on a
+2048 (r) x 4096 (z) grid, seeded log-uniform conductivities, uniform heat
+capacities and heater source, dt = 50 x the explicit stability limit; one
+bench step = one ADI time step (r-sweep + z-sweep).  The FP32 path is the
+headline (`value`); the FP64 path is measured side by side.
+
+Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
+(a 512 MB device write) and bracketed by CUDA events on the solver's stream,
+with an event between the two sweeps for per-kernel durations.
+`value` = active cells x K / (sum of step times).  `e2e` runs the same job
+through the C ABI with host buffers: upload of the initial field, K steps,
+download of the result, timed as a whole.
+
+--impl reference times the FP64 CPU oracle (the method's plain restatement,
+OpenMP over lines as in the paper's Sec. 4) on a bounded number of steps of
+the same workload.  Multi-GPU (torchrun): every rank runs an independent
+replica (the single-domain solve does not shard); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import heat as H  # noqa: E402
+
+METRIC = "cell-steps/s vs HBM roofline"
+UNIT = "cell-steps/s"
+WORKLOAD = "config2: five-region layered cell 2048x4096, seed 2, dt=50*tau_exp"
+ELEM = {"fp64": 8, "fp32": 4}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_gpu(p, precision, steps, warmup, flush):
+    """Per-step CUDA-event timing of the two sweeps with an L2 flush before each step."""
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver
+    probe = HeatSolver(p, 1.0, precision=precision)
+    tau = H.DT_FACTOR * probe.tau_exp
+    probe.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = HeatSolver(p, tau, precision=precision, stream=stream)
+        s.step(warmup)
+        n = steps
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            s.sweep(0)
+            ev[k][1].record(stream)
+            s.sweep(1)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    r_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(n)]
+    z_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(n)]
+    E, Phi, Q = s.energy()
+    launches = s.launches_per_step() * n
+    s.close()
+    return dict(tau=tau, r_ms=r_ms, z_ms=z_ms, wall=wall, launches=launches, E=E)
+
+
+def time_e2e(p, precision, steps):
+    """One job through the C ABI with host buffers: upload, K steps, download."""
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver
+    probe = HeatSolver(p, 1.0, precision=precision)
+    tau = H.DT_FACTOR * probe.tau_exp
+    probe.close()
+    s = HeatSolver(p, tau, precision=precision)
+    T0 = np.full((p.Nz, p.Nr), p.T_init)
+    s.set_field(T0)
+    s.step(2)
+    s.field()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_field(T0)
+    s.step(steps)
+    out = s.field()
+    t1 = time.perf_counter()
+    s.close()
+    assert np.isfinite(out).all()
+    nbytes = p.Nr * p.Nz * ELEM[precision]
+    return t1 - t0, nbytes
+
+
+def active_cells(p):
+    from oracle import Oracle  # grid region map only, for counting
+    o = Oracle(p)
+    n = int((o.grid()["region"] >= 0).sum())
+    del o
+    return n
+
+
+def cpu_baseline(p, budget_s=12.0, max_steps=50):
+    """The FP64 oracle as it stands, all host cores, bounded number of steps."""
+    import oracle
+    from oracle import Oracle
+    o = Oracle(p)
+    tau = H.DT_FACTOR * o.tau_exp()
+    cores = oracle.max_threads()
+    o.step(tau, 1)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps and (time.perf_counter() - t0) < budget_s:
+        o.step(tau, 1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n, dt, cores
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    p = H.config2()
+    act = active_cells(p)
+    n, dt, cores = cpu_baseline(p, budget_s=max(5.0, 0.5 * args.steps), max_steps=max(1, args.steps))
+    v = act * n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": n, "warmup": 1, "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [p.Nr, p.Nz], "precision": "fp64", "solver": "cpu oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} steps of the full 2048x4096 workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nr", type=int, default=2048)
+    ap.add_argument("--nz", type=int, default=4096)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+
+    p = H.config2(args.nr, args.nz)
+    act = active_cells(p)
+    ncell = p.Nr * p.Nz
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    other = "fp64" if args.precision == "fp32" else "fp32"
+
+    _barrier(ws)
+    with Clocks(local) as clk:
+        main_t = time_gpu(p, args.precision, args.steps, args.warmup, flush)
+    side_steps = max(3, min(args.steps, 200))
+    side_t = time_gpu(p, other, side_steps, args.warmup, flush)
+    e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
+    _barrier(ws)
+
+    tot_ms = sum(main_t["r_ms"]) + sum(main_t["z_ms"])
+    tot_ms = _reduce_max(tot_ms, ws)
+    e2e_s = _reduce_max(e2e_s, ws)
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    value = ws * act * args.steps / (tot_ms * 1e-3)
+
+    def roof(t, precision):
+        r_avg = statistics.mean(t["r_ms"])
+        z_avg = statistics.mean(t["z_ms"])
+        name, avg = ("rsweep", r_avg) if r_avg >= z_avg else ("zsweep", z_avg)
+        bytes_launch = 2 * ELEM[precision] * ncell  # read + write of every cell per sweep
+        ach = bytes_launch / (avg * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                "rsweep_ms": r_avg, "zsweep_ms": z_avg}
+
+    side_ms = (sum(side_t["r_ms"]) + sum(side_t["z_ms"])) / len(side_t["r_ms"])
+    cpu = None
+    if not args.no_cpu_baseline:
+        n, dt, cores = cpu_baseline(p)
+        cpu = {"value": act * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} steps of the full {p.Nr}x{p.Nz} workload"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [p.Nr, p.Nz], "precision": args.precision,
+                   "active_cells": act, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof(main_t, args.precision),
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * act * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": e2e_bytes / args.steps, "d2h_bytes_per_step": e2e_bytes / args.steps},
+        "gpu_launches": main_t["launches"],
+        "clocks": clk.summary(),
+        "side_by_side": {other: {"value": act / (side_ms * 1e-3), "ms_per_step": side_ms,
+                                 "steps": len(side_t["r_ms"]), "roofline": roof(side_t, other)}},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * heat.h -- C ABI of libheat.so: the per-time-step implicit (ADI) solve of the
+ * axisymmetric (r,z) heat equation in a cylinder made of piecewise-constant
+ * material regions, on one GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 1912.03744, "Parallel Algorithm for Numerical Solution of Heat
+ * Equation in Complex Cylindrical Domain"):
+ *   Sec. 2, eq. "main_eq"     C dT/dt = (1/r) d/dr(r k dT/dr) + d/dz(k dT/dz) + X
+ *                             with k, C = rho c_V and X constant per region.
+ *   Sec. 2, eq. "boundcond"   dT/dn = 0 on the boundary except T = T0 on the top
+ *                             face; no flux through the axis.  Here each outer
+ *                             face (r_lo, r_hi, z_lo, z_hi) is Neumann or Dirichlet.
+ *   Sec. 3, eq. "grid"        shifted (cell-centred) grid, uniform inside a layer.
+ *   Sec. 3, eqs. "Lambda_r", "Lambda_z" and their definitions: the spatial
+ *                             operators with the 1/r metric and face conductivities.
+ *   Sec. 3, eqs. "scheme_eq_1", "scheme_eq_2": one step = half-step 1 (implicit
+ *                             in r, explicit in z) then half-step 2 (explicit in
+ *                             r, implicit in z), each of length tau/2.
+ *   Sec. 3, last paragraph before Sec. 4: every implicit system is a set of
+ *                             independent tridiagonal line systems (Thomas).
+ * Readings of silent or garbled points: mirror ghost cells at outer faces
+ * (h_0 = 2 (r_0 - r_lo), r_{-1/2} = r_lo, zero at the axis); harmonic face
+ * conductivity weighted by cell half widths (HEAT_HARMONIC, default) or the
+ * literal arithmetic mean (HEAT_ARITH); Dirichlet flux k (T_bc - T)/(dx/2);
+ * void cells (no box) are identity rows with insulated faces.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HEAT_OK (0) or a negative HEAT_ERR_* code; nothing throws
+ *     across the ABI.  heat_strerror() names a code.
+ *   - Units: SI (m, s, K, W/(m K), J/(m^3 K), W/m^3).
+ *   - Field layout: row-major [Nz][Nr] doubles, index j*Nr + i, i the radial
+ *     cell (fastest), j the axial cell.
+ *   - Ownership: the library allocates and owns every device buffer of a
+ *     context; caller buffers are only read or written during the call
+ *     (host pointers) or in stream order on the context's stream (device
+ *     pointers, on_device = 1).
+ *   - Streams: work is enqueued on the stream given to heat_create (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     heat_step is asynchronous; calls that return host data synchronize.
+ */
+#ifndef HEAT_H
+#define HEAT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HEAT_OK 0
+#define HEAT_ERR_ARG (-1)       /* invalid argument (sizes, ordering, dt <= 0, NULL) */
+#define HEAT_ERR_CUDA (-2)      /* a CUDA runtime call or kernel launch failed      */
+#define HEAT_ERR_NONFINITE (-3) /* the field holds NaN or Inf (found by heat_energy) */
+#define HEAT_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up               */
+#define HEAT_ERR_OOM (-5)       /* device allocation failed                         */
+
+/* ---- precision of the stored field and the line solves ---- */
+#define HEAT_FP64 0             /* FP64 field, FP64 line solves                     */
+#define HEAT_FP32 1             /* FP32 field (offset by T_init), FP32 line solves  */
+#define HEAT_FP32_REFINED 2     /* FP32 field and solves + one FP64-residual
+                                   correction solve per line (iterative refinement) */
+
+/* ---- face conductivity at a material interface (garbled in Sec. 3) ---- */
+#define HEAT_HARMONIC 0
+#define HEAT_ARITH 1
+
+/* ---- boundary condition kinds ---- */
+#define HEAT_BC_NEUMANN 0
+#define HEAT_BC_DIRICHLET 1
+
+typedef struct heat_ctx heat_ctx; /* opaque, library-owned */
+
+/* Axis-aligned region box in (r,z): a cell belongs to the first box whose
+ * closed rectangle contains its centre; cells in no box are void. */
+typedef struct {
+    double r0, r1, z0, z1;
+    int region; /* index into heat_materials arrays */
+} heat_box;
+
+/* Layered geometry (Sec. 3, eq. "grid"): radial layers [r_faces[l], r_faces[l+1]]
+ * of r_cells[l] uniform cells each, axial segments likewise.  r_faces[0] = 0 is
+ * the symmetry axis (its face carries no flux whatever bc[0] says).
+ * bc[f], T_bc[f]: kind and value on faces f = 0 r_lo, 1 r_hi, 2 z_lo, 3 z_hi. */
+typedef struct {
+    int n_r_layers;
+    const double *r_faces; /* n_r_layers + 1, strictly increasing, >= 0 */
+    const int *r_cells;    /* n_r_layers, each >= 1                      */
+    int n_z_layers;
+    const double *z_faces; /* n_z_layers + 1, strictly increasing        */
+    const int *z_cells;    /* n_z_layers, each >= 1                      */
+    int n_boxes;           /* 1..32                                       */
+    const heat_box *boxes;
+    int bc[4];
+    double T_bc[4];
+} heat_geometry;
+
+/* Per-region constants (the paper's k(T), c_V(T), rho(r), X(T) read as constants). */
+typedef struct {
+    int n_regions;
+    const double *k; /* conductivity > 0                 */
+    const double *C; /* volumetric heat capacity > 0     */
+    const double *q; /* volumetric source (any sign)     */
+    double T_init;   /* uniform initial temperature (eq. "initcond") */
+} heat_materials;
+
+typedef struct {
+    int precision; /* HEAT_FP64 | HEAT_FP32 | HEAT_FP32_REFINED */
+    int face_mean; /* HEAT_HARMONIC | HEAT_ARITH                 */
+} heat_options;
+
+/* Build the grid, region map, per-line-class coefficient and factorization
+ * tables for time step dt (> 0), allocate device buffers, set T = T_init.
+ * stream: cudaStream_t as void* (NULL = legacy default stream).
+ * Errors: HEAT_ERR_ARG (bad sizes, ordering, counts, dt <= 0, NULL pointers),
+ * HEAT_ERR_OOM, HEAT_ERR_CUDA.  On error *out is NULL. */
+int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat_options *opt,
+                double dt, void *stream, heat_ctx **out);
+
+/* Change the time step (rebuilds the factorization tables).  dt > 0. */
+int heat_set_dt(heat_ctx *ctx, double dt);
+
+/* Enqueue n >= 0 ADI steps (eqs. "scheme_eq_1" then "scheme_eq_2" per step)
+ * on the context stream.  Asynchronous; launch errors return HEAT_ERR_CUDA. */
+int heat_step(heat_ctx *ctx, int n);
+
+/* One half-step only: dir = 0 runs half-step 1 (eq. "scheme_eq_1": implicit
+ * in r, explicit in z), after which the current field is the half layer
+ * Tbar; dir = 1 then runs half-step 2 (eq. "scheme_eq_2") to the next layer.
+ * heat_step(ctx, 1) equals heat_sweep(ctx, 0) followed by heat_sweep(ctx, 1).
+ * Errors: HEAT_ERR_ARG if dir is not 0/1, if dir = 1 is called without a
+ * preceding dir = 0, or if dir = 0 is called twice in a row; heat_step
+ * returns HEAT_ERR_ARG while a half-step is pending. */
+int heat_sweep(heat_ctx *ctx, int dir);
+
+/* Copy the current temperature field (Nz*Nr doubles, [j][i]) to out; n must
+ * equal Nr*Nz.  on_device = 0: out is host memory, the call synchronizes.
+ * on_device = 1: out is device memory, the copy is stream-ordered. */
+int heat_field(heat_ctx *ctx, double *out, size_t n, int on_device);
+
+/* Replace the field (restart / resume); same layout and rules as heat_field.
+ * Void cells keep whatever value is given. */
+int heat_set_field(heat_ctx *ctx, const double *in, size_t n, int on_device);
+
+/* FP64 reductions of the current field (synchronizes):
+ *   E   = 2 pi sum_active C T r_i hbar_i etabar_j        (J)
+ *   Phi = 2 pi sum over Dirichlet faces of r_i hbar_i etabar_j D (T_bc - T)  (W, into Omega)
+ *   Q   = 2 pi sum_active q r_i hbar_i etabar_j          (W)
+ * With only the top face Dirichlet, one step satisfies
+ *   E(next) - E(now) = tau Q + (tau/2) (Phi(now) + Phi(next)).
+ * Any pointer may be NULL.  Returns HEAT_ERR_NONFINITE if E or Phi is not finite. */
+int heat_energy(heat_ctx *ctx, double *E, double *Phi, double *Q);
+
+/* Grid and limits.  Any pointer may be NULL; r_centres holds Nr, z_centres Nz
+ * doubles.  tau_exp = min over active cells of C / (sum of the cell's
+ * couplings), the forward-Euler positivity limit of the assembled operator. */
+int heat_info(heat_ctx *ctx, int *Nr, int *Nz, double *r_centres, double *z_centres,
+              double *tau_exp);
+
+/* Number of kernel launches heat_step(ctx, 1) enqueues (for launch accounting). */
+int heat_launches_per_step(heat_ctx *ctx);
+
+/* Wait for the context stream; returns the first deferred error, if any. */
+int heat_sync(heat_ctx *ctx);
+
+void heat_destroy(heat_ctx *ctx);
+
+const char *heat_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEAT_H */

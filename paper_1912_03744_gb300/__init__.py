@@ -1,0 +1,6 @@
+"""GB300-native (sm_103a) ADI heat solver for layered axisymmetric cylinders.
+
+The compute path is libheat.so (CUDA kernels behind the C ABI in
+include/heat.h); this package is its thin Python binding.
+"""
+from .heat import HeatSolver, HeatError, load, LIB_PATH, SYMBOLS  # noqa: F401

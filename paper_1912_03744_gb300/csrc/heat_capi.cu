@@ -1,0 +1,292 @@
+// heat_capi.cu -- the extern "C" entry points of libheat.so (declared and
+// documented in include/heat.h).  Host-side orchestration only: every cell
+// of every step is computed by the kernels in heat_sweeps.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "heat_internal.h"
+
+namespace heat {
+int validate(const heat_geometry *, const heat_materials *, const heat_options *, double);
+void build_grid(const heat_geometry *, Grid &);
+void build_tables(heat_ctx *);
+void compute_limits(heat_ctx *);
+cudaError_t launch_steps(heat_ctx *, int);
+cudaError_t launch_sweep(heat_ctx *, int);
+cudaError_t launch_energy(heat_ctx *);
+cudaError_t launch_theta_to_T(heat_ctx *, double *);
+cudaError_t launch_T_to_theta(heat_ctx *, const double *);
+int launches_per_step(const heat_ctx *);
+int energy_blocks(const heat_ctx *);
+}  // namespace heat
+
+using namespace heat;
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return HEAT_OK;
+    if (e == cudaErrorMemoryAllocation) return HEAT_ERR_OOM;
+    return HEAT_ERR_CUDA;
+}
+
+#define HEAT_CHECK(call)                            \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+constexpr int kFields64 = 18;
+constexpr int kFields32 = 12;
+
+// Upload one direction's host tables: FP64 master (18 fields) and, for the
+// FP32 paths, an FP32 copy of the 12 fields the sweeps use.
+int upload_tab(heat_ctx *ctx, const HostTab &T, DevTab &D)
+{
+    const size_t n = (size_t)T.n_class * T.N;
+    if (!D.buf64) HEAT_CHECK(cudaMalloc(&D.buf64, kFields64 * n * sizeof(double)));
+    const std::vector<double> *src[kFields64] = {&T.inv, &T.f,  &T.cp, &T.w,  &T.s, &T.am,  &T.ap,   &T.ad,  &T.sd,
+                                                 &T.dl,  &T.dh, &T.q,  &T.m,  &T.b, &T.p,   &T.cap, &T.dsum, &T.dbc};
+    std::vector<double> host(kFields64 * n);
+    for (int a = 0; a < kFields64; ++a) std::memcpy(host.data() + a * n, src[a]->data(), n * sizeof(double));
+    HEAT_CHECK(cudaMemcpyAsync(D.buf64, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    double *p = D.buf64;
+    auto F = [&](int a) { return (const double *)(p + a * n); };
+    D.t64 = LineTab<double>{F(0), F(1), F(2), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11)};
+    D.full = LineTab64{F(12), F(13), F(14), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11),
+                       F(15), F(16), F(17)};
+    if (ctx->precision != HEAT_FP64) {
+        if (!D.buf32) HEAT_CHECK(cudaMalloc(&D.buf32, kFields32 * n * sizeof(float)));
+        std::vector<float> h32(kFields32 * n);
+        for (size_t x = 0; x < kFields32 * n; ++x) h32[x] = (float)host[x];
+        HEAT_CHECK(cudaMemcpyAsync(D.buf32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+        float *q = D.buf32;
+        auto G = [&](int a) { return (const float *)(q + a * n); };
+        D.t32 = LineTab<float>{G(0), G(1), G(2), G(3), G(4), G(5), G(6), G(7), G(8), G(9), G(10), G(11)};
+    }
+    // host vectors are freed on return: the copies must complete first
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    return HEAT_OK;
+}
+
+void free_ctx(heat_ctx *ctx)
+{
+    if (!ctx) return;
+    void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32, ctx->dZ.buf64, ctx->dZ.buf32, ctx->d_rowcls, ctx->d_colcls,
+                    ctx->d_wr,     ctx->d_wz,     ctx->d_field[0], ctx->d_field[1], ctx->d_part, ctx->d_res};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete ctx;
+}
+
+size_t elem_size(const heat_ctx *ctx) { return ctx->precision == HEAT_FP64 ? sizeof(double) : sizeof(float); }
+
+}  // namespace
+
+extern "C" {
+
+const char *heat_strerror(int status)
+{
+    switch (status) {
+    case HEAT_OK: return "ok";
+    case HEAT_ERR_ARG: return "invalid argument";
+    case HEAT_ERR_CUDA: return "CUDA error";
+    case HEAT_ERR_NONFINITE: return "non-finite field";
+    case HEAT_ERR_TIMEOUT: return "device wait timed out";
+    case HEAT_ERR_OOM: return "device out of memory";
+    default: return "unknown status";
+    }
+}
+
+int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat_options *opt, double dt,
+                void *stream, heat_ctx **out)
+{
+    if (!out) return HEAT_ERR_ARG;
+    *out = nullptr;
+    int st = validate(geom, mat, opt, dt);
+    if (st != HEAT_OK) return st;
+    heat_ctx *ctx = new (std::nothrow) heat_ctx();
+    if (!ctx) return HEAT_ERR_OOM;
+    ctx->precision = opt->precision;
+    ctx->face_mean = opt->face_mean;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    // FP32 fields hold theta = T - T_init (precision where T varies little
+    // around T_init); the FP64 field holds T itself, so a checkpoint through
+    // heat_field / heat_set_field is lossless in every precision.
+    ctx->T_ref = opt->precision == HEAT_FP64 ? 0.0 : mat->T_init;
+    for (int f = 0; f < 4; ++f) {
+        ctx->bc[f] = geom->bc[f];
+        ctx->theta_bc[f] = geom->T_bc[f] - ctx->T_ref;
+    }
+    ctx->box_region.resize(geom->n_boxes);
+    for (int b = 0; b < geom->n_boxes; ++b) ctx->box_region[b] = geom->boxes[b].region;
+    ctx->k.assign(mat->k, mat->k + mat->n_regions);
+    ctx->C.assign(mat->C, mat->C + mat->n_regions);
+    ctx->q.assign(mat->q, mat->q + mat->n_regions);
+    ctx->tau = dt;
+    build_grid(geom, ctx->g);
+    build_tables(ctx);
+    compute_limits(ctx);
+
+    const Grid &g = ctx->g;
+    const size_t ncell = (size_t)g.Nr * g.Nz;
+    auto fail = [&](int s) {
+        free_ctx(ctx);
+        return s;
+    };
+    if ((st = upload_tab(ctx, ctx->R, ctx->dR)) != HEAT_OK) return fail(st);
+    if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return fail(st);
+    std::vector<double> wr(g.Nr), wz(g.Nz);
+    for (int i = 0; i < g.Nr; ++i) wr[i] = 2.0 * kPi * g.rc[i] * g.hbar[i];
+    for (int j = 0; j < g.Nz; ++j) wz[j] = g.etabar[j];
+    cudaError_t e;
+#define HEAT_TRY(call)                                   \
+    if ((e = (call)) != cudaSuccess) return fail(cuda_status(e))
+    HEAT_TRY(cudaMalloc(&ctx->d_rowcls, g.Nz * sizeof(int)));
+    HEAT_TRY(cudaMalloc(&ctx->d_colcls, g.Nr * sizeof(int)));
+    HEAT_TRY(cudaMalloc(&ctx->d_wr, g.Nr * sizeof(double)));
+    HEAT_TRY(cudaMalloc(&ctx->d_wz, g.Nz * sizeof(double)));
+    HEAT_TRY(cudaMalloc(&ctx->d_field[0], ncell * elem_size(ctx)));
+    HEAT_TRY(cudaMalloc(&ctx->d_field[1], ncell * elem_size(ctx)));
+    ctx->n_part = energy_blocks(ctx);
+    HEAT_TRY(cudaMalloc(&ctx->d_part, 2 * ctx->n_part * sizeof(double)));
+    HEAT_TRY(cudaMalloc(&ctx->d_res, 2 * sizeof(double)));
+    HEAT_TRY(cudaMemcpyAsync(ctx->d_rowcls, g.rowcls.data(), g.Nz * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_TRY(cudaMemcpyAsync(ctx->d_colcls, g.colcls.data(), g.Nr * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_TRY(cudaMemcpyAsync(ctx->d_wr, wr.data(), g.Nr * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_TRY(cudaMemcpyAsync(ctx->d_wz, wz.data(), g.Nz * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_TRY(cudaMemsetAsync(ctx->d_field[1], 0, ncell * elem_size(ctx), ctx->stream));
+    if (ctx->T_ref == mat->T_init) {
+        // theta = T - T_ref = 0 everywhere at T = T_init (eq. "initcond")
+        HEAT_TRY(cudaMemsetAsync(ctx->d_field[0], 0, ncell * elem_size(ctx), ctx->stream));
+    } else {
+        HEAT_TRY(cudaStreamSynchronize(ctx->stream));
+        std::vector<double> init(ncell, mat->T_init);
+        int s2 = heat_set_field(ctx, init.data(), ncell, 0);
+        if (s2 != HEAT_OK) return fail(s2);
+    }
+    HEAT_TRY(cudaStreamSynchronize(ctx->stream));
+#undef HEAT_TRY
+    *out = ctx;
+    return HEAT_OK;
+}
+
+int heat_set_dt(heat_ctx *ctx, double dt)
+{
+    if (!ctx || !(dt > 0.0) || !std::isfinite(dt)) return HEAT_ERR_ARG;
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->tau = dt;
+    build_tables(ctx);
+    int st = upload_tab(ctx, ctx->R, ctx->dR);
+    if (st != HEAT_OK) return st;
+    return upload_tab(ctx, ctx->Z, ctx->dZ);
+}
+
+int heat_sweep(heat_ctx *ctx, int dir)
+{
+    if (!ctx || (dir != 0 && dir != 1)) return HEAT_ERR_ARG;
+    if ((dir == 1) != (ctx->half == 1)) return HEAT_ERR_ARG;
+    int st = cuda_status(launch_sweep(ctx, dir));
+    if (st != HEAT_OK) return st;
+    ctx->cur = 1 - ctx->cur;
+    ctx->half = dir == 0 ? 1 : 0;
+    return HEAT_OK;
+}
+
+int heat_step(heat_ctx *ctx, int n)
+{
+    if (!ctx || n < 0 || ctx->half) return HEAT_ERR_ARG;
+    if (n == 0) return HEAT_OK;
+    return cuda_status(launch_steps(ctx, n));
+}
+
+int heat_field(heat_ctx *ctx, double *out, size_t n, int on_device)
+{
+    if (!ctx || !out) return HEAT_ERR_ARG;
+    const size_t ncell = (size_t)ctx->g.Nr * ctx->g.Nz;
+    if (n != ncell) return HEAT_ERR_ARG;
+    if (on_device) return cuda_status(launch_theta_to_T(ctx, out));
+    if (ctx->precision == HEAT_FP64) {
+        HEAT_CHECK(cudaMemcpyAsync(out, ctx->d_field[ctx->cur], ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (size_t c = 0; c < ncell; ++c) out[c] += ctx->T_ref;
+    } else {
+        std::vector<float> tmp(ncell);
+        HEAT_CHECK(cudaMemcpyAsync(tmp.data(), ctx->d_field[ctx->cur], ncell * sizeof(float), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (size_t c = 0; c < ncell; ++c) out[c] = (double)tmp[c] + ctx->T_ref;
+    }
+    return HEAT_OK;
+}
+
+int heat_set_field(heat_ctx *ctx, const double *in, size_t n, int on_device)
+{
+    if (!ctx || !in) return HEAT_ERR_ARG;
+    const size_t ncell = (size_t)ctx->g.Nr * ctx->g.Nz;
+    if (n != ncell) return HEAT_ERR_ARG;
+    if (on_device) return cuda_status(launch_T_to_theta(ctx, in));
+    if (ctx->precision == HEAT_FP64) {
+        std::vector<double> tmp(ncell);
+        for (size_t c = 0; c < ncell; ++c) tmp[c] = in[c] - ctx->T_ref;
+        HEAT_CHECK(cudaMemcpyAsync(ctx->d_field[ctx->cur], tmp.data(), ncell * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::vector<float> tmp(ncell);
+        for (size_t c = 0; c < ncell; ++c) tmp[c] = (float)(in[c] - ctx->T_ref);
+        HEAT_CHECK(cudaMemcpyAsync(ctx->d_field[ctx->cur], tmp.data(), ncell * sizeof(float), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    return HEAT_OK;
+}
+
+int heat_energy(heat_ctx *ctx, double *E, double *Phi, double *Q)
+{
+    if (!ctx) return HEAT_ERR_ARG;
+    HEAT_CHECK(launch_energy(ctx));
+    double res[2];
+    HEAT_CHECK(cudaMemcpyAsync(res, ctx->d_res, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream));
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (E) *E = res[0] + ctx->E_ref;
+    if (Phi) *Phi = res[1];
+    if (Q) *Q = ctx->Q;
+    if (!std::isfinite(res[0]) || !std::isfinite(res[1])) return HEAT_ERR_NONFINITE;
+    return HEAT_OK;
+}
+
+int heat_info(heat_ctx *ctx, int *Nr, int *Nz, double *r_centres, double *z_centres, double *tau_exp)
+{
+    if (!ctx) return HEAT_ERR_ARG;
+    if (Nr) *Nr = ctx->g.Nr;
+    if (Nz) *Nz = ctx->g.Nz;
+    if (r_centres) std::memcpy(r_centres, ctx->g.rc.data(), ctx->g.Nr * sizeof(double));
+    if (z_centres) std::memcpy(z_centres, ctx->g.zc.data(), ctx->g.Nz * sizeof(double));
+    if (tau_exp) *tau_exp = ctx->tau_exp;
+    return HEAT_OK;
+}
+
+int heat_launches_per_step(heat_ctx *ctx) { return ctx ? launches_per_step(ctx) : HEAT_ERR_ARG; }
+
+int heat_sync(heat_ctx *ctx)
+{
+    if (!ctx) return HEAT_ERR_ARG;
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    return ctx->deferred;
+}
+
+void heat_destroy(heat_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+}  // extern "C"

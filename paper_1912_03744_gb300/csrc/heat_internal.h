@@ -1,0 +1,110 @@
+// heat_internal.h -- data structures shared by the host setup, the C ABI and
+// the CUDA kernels of libheat.so.
+//
+// Line classes.  The region map of a layered cell is a function of two masks:
+// the set of boxes whose r-range contains the radial centre r_i (maskR[i]) and
+// the set whose z-range contains the axial centre z_j (maskZ[j]).  Every row j
+// with the same maskZ therefore has the same region vector over i, hence the
+// same tridiagonal r-line matrix (Sec. 3, eq. "scheme_eq_1"); every column
+// with the same maskR has the same z-line matrix (eq. "scheme_eq_2").  The
+// library builds one coefficient table per row class (length Nr) and one per
+// column class (length Nz) instead of per-cell coefficient arrays, so the
+// sweeps read O(Nr + Nz) table entries, not O(Nr Nz), and the Thomas
+// factorization (pivots) of each class is computed once per dt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "heat.h"
+
+namespace heat {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// One direction's per-class tables, structure of arrays, [n_class][N].
+//   inv, f, cp : factorization of the implicit line matrix
+//                -m_i x_{i-1} + b_i x_i - p_i x_{i+1} = d_i  (m, p >= 0):
+//                den_0 = b_0, den_i = b_i - m_i cp_{i-1}, inv = 1/den,
+//                f = m/den, cp = p/den, so the Thomas recurrences are
+//                d'_i = d_i inv_i + f_i d'_{i-1},  x_i = d'_i + cp_i x_{i+1}.
+//   w, s       : right-hand side of this direction's implicit half-step in
+//                the literal form: mass term 2C/tau (1 on void) and the
+//                source q + D_face theta_bc of this direction's Dirichlet faces.
+//   am, ap, ad, sd : this direction's operator applied explicitly by the
+//                other half-step:  am x_{-} + ap x_{+} + ad x + sd
+//                (ad = -(m + p + D), sd = D theta_bc).
+//   dl, dh, q  : Dirichlet coefficient of the low / high outer face (0 off the
+//                face) and the volumetric source (0 on void), used by the
+//                increment form (see heat_sweeps.cu).
+//   m, b, p    : the matrix itself (FP64 only; residuals of the refined path).
+//   cap, dsum, dbc : FP64 energy/flux weights: C (0 on void), sum of the
+//                Dirichlet coefficients D of this direction and D theta_bc.
+template <typename real>
+struct LineTab {
+    const real *inv, *f, *cp, *w, *s, *am, *ap, *ad, *sd, *dl, *dh, *q;
+};
+
+struct LineTab64 {
+    const double *m, *b, *p, *w, *s, *am, *ap, *ad, *sd, *dl, *dh, *q;
+    const double *cap, *dsum, *dbc;
+};
+
+// Host FP64 master of one direction's tables.
+struct HostTab {
+    int n_class = 0, N = 0;
+    std::vector<double> inv, f, cp, w, s, am, ap, ad, sd, dl, dh, q, m, b, p, cap, dsum, dbc;
+    std::vector<double> ssum;  // sum of all couplings (for tau_exp)
+    void resize(int nc, int n);
+};
+
+// Device copy of one direction's tables (FP64 always; FP32 copy when needed).
+struct DevTab {
+    double *buf64 = nullptr;  // 18 fields x n_class x N doubles
+    float *buf32 = nullptr;   // 12 fields x n_class x N floats
+    LineTab<double> t64{};
+    LineTab<float> t32{};
+    LineTab64 full{};
+};
+
+struct Grid {
+    int Nr = 0, Nz = 0;
+    double r_lo = 0, r_hi = 0, z_lo = 0, z_hi = 0;
+    std::vector<double> rc, dr, h, hbar, rf;  // radial: centres, widths, h[0..Nr], hbar, r_{i-1/2}[0..Nr]
+    std::vector<double> zc, dz, eta, etabar;  // axial
+    std::vector<uint32_t> maskR, maskZ;       // boxes containing each centre, per axis
+    std::vector<int> rowcls, colcls;          // class of each row j / column i
+    std::vector<uint32_t> rowmask, colmask;   // maskZ of each row class / maskR of each column class
+};
+
+}  // namespace heat
+
+struct heat_ctx {
+    int precision = HEAT_FP64;
+    int face_mean = HEAT_HARMONIC;
+    cudaStream_t stream = nullptr;
+    heat::Grid g;
+    // problem constants
+    double T_ref = 0.0;        // field stored as theta = T - T_ref
+    double theta_bc[4] = {0, 0, 0, 0};
+    int bc[4] = {0, 0, 0, 0};
+    std::vector<int> box_region;
+    std::vector<double> k, C, q;
+    double tau = 0.0, tau_exp = 0.0;
+    double E_ref = 0.0, Q = 0.0;  // 2 pi sum C T_ref r hbar etabar; source power
+    heat::HostTab R, Z;
+    // device
+    heat::DevTab dR, dZ;
+    int *d_rowcls = nullptr, *d_colcls = nullptr;
+    double *d_wr = nullptr, *d_wz = nullptr;  // energy weights 2 pi r_i hbar_i, etabar_j
+    void *d_field[2] = {nullptr, nullptr};
+    int cur = 0;                  // index of the buffer holding the current field
+    int half = 0;                 // 1 after heat_sweep(ctx, 0): the current field is Tbar
+    double *d_part = nullptr;     // per-block energy partials (scratch)
+    double *d_res = nullptr;      // [E_theta, Phi]
+    double *d_tmp64 = nullptr;    // Nr*Nz doubles for host/device transfers of FP32 fields
+    int n_part = 0;
+    int deferred = HEAT_OK;
+};

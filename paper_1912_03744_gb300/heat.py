@@ -1,0 +1,211 @@
+"""Thin ctypes binding of libheat.so (C ABI declared in include/heat.h).
+
+Argument marshalling only: every step of the ADI path runs in the library's
+CUDA kernels.  PyTorch is used for device buffers and streams.  There is no
+CPU fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libheat.so")
+
+HEAT_OK = 0
+STATUS = {0: "ok", -1: "HEAT_ERR_ARG", -2: "HEAT_ERR_CUDA", -3: "HEAT_ERR_NONFINITE",
+          -4: "HEAT_ERR_TIMEOUT", -5: "HEAT_ERR_OOM"}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
+NUMPY_DTYPE = {"fp64": np.float64, "fp32": np.float32, "fp32_refined": np.float32}
+
+# Every extern "C" symbol include/heat.h declares.
+SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field", "heat_set_field", "heat_energy",
+           "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror"]
+
+
+class HeatError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("r0", ctypes.c_double), ("r1", ctypes.c_double), ("z0", ctypes.c_double),
+                ("z1", ctypes.c_double), ("region", ctypes.c_int)]
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("n_r_layers", ctypes.c_int), ("r_faces", ctypes.POINTER(ctypes.c_double)),
+                ("r_cells", ctypes.POINTER(ctypes.c_int)),
+                ("n_z_layers", ctypes.c_int), ("z_faces", ctypes.POINTER(ctypes.c_double)),
+                ("z_cells", ctypes.POINTER(ctypes.c_int)),
+                ("n_boxes", ctypes.c_int), ("boxes", ctypes.POINTER(_Box)),
+                ("bc", ctypes.c_int * 4), ("T_bc", ctypes.c_double * 4)]
+
+
+class _Materials(ctypes.Structure):
+    _fields_ = [("n_regions", ctypes.c_int), ("k", ctypes.POINTER(ctypes.c_double)),
+                ("C", ctypes.POINTER(ctypes.c_double)), ("q", ctypes.POINTER(ctypes.c_double)),
+                ("T_init", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("face_mean", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libheat.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        L.heat_create.argtypes = [ctypes.POINTER(_Geometry), ctypes.POINTER(_Materials), ctypes.POINTER(_Options),
+                                  ctypes.c_double, vp, ctypes.POINTER(vp)]
+        L.heat_set_dt.argtypes = [vp, ctypes.c_double]
+        L.heat_step.argtypes = [vp, ctypes.c_int]
+        L.heat_sweep.argtypes = [vp, ctypes.c_int]
+        L.heat_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.heat_set_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.heat_energy.argtypes = [vp, dp, dp, dp]
+        L.heat_info.argtypes = [vp, ip, ip, dp, dp, dp]
+        L.heat_launches_per_step.argtypes = [vp]
+        L.heat_sync.argtypes = [vp]
+        L.heat_destroy.argtypes = [vp]
+        L.heat_destroy.restype = None
+        L.heat_strerror.argtypes = [ctypes.c_int]
+        L.heat_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(fn, st):
+    if st != HEAT_OK:
+        raise HeatError(fn, st)
+
+
+def _current_stream_handle():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class HeatSolver:
+    """One ADI heat problem on the GPU (wraps heat_create / heat_step / ...).
+
+    ``problem`` is any object with the attributes of ``workloads.heat.Problem``
+    (r_faces, r_cells, z_faces, z_cells, boxes, box_region, bc, T_bc, k, C, q,
+    T_init, face_mean).  ``stream``: a torch.cuda.Stream, or None for torch's
+    current stream.
+    """
+
+    def __init__(self, problem, dt: float, precision: str = "fp64", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("HeatSolver needs a CUDA GPU; there is no CPU path")
+        L = load()
+        p = problem
+        self._keep = []
+
+        def arr(x, dt_):
+            a = np.ascontiguousarray(x, dtype=dt_)
+            self._keep.append(a)
+            return a
+
+        rf, rc = arr(p.r_faces, np.float64), arr(p.r_cells, np.int32)
+        zf, zc = arr(p.z_faces, np.float64), arr(p.z_cells, np.int32)
+        bx = np.asarray(p.boxes, dtype=np.float64).reshape(-1, 4)
+        boxes = (_Box * len(bx))(*[_Box(*map(float, b), int(r)) for b, r in zip(bx, p.box_region)])
+        self._keep.append(boxes)
+        geo = _Geometry(len(rc), rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        rc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        len(zc), zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        zc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(bx), boxes,
+                        (ctypes.c_int * 4)(*[int(v) for v in p.bc]),
+                        (ctypes.c_double * 4)(*[float(v) for v in p.T_bc]))
+        k, C, q = arr(p.k, np.float64), arr(p.C, np.float64), arr(p.q, np.float64)
+        mat = _Materials(len(k), k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(p.T_init))
+        opt = _Options(PRECISION[precision], int(getattr(p, "face_mean", 0)))
+        self.stream = stream
+        sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _current_stream_handle()
+        h = ctypes.c_void_p()
+        _check("heat_create", L.heat_create(ctypes.byref(geo), ctypes.byref(mat), ctypes.byref(opt),
+                                            float(dt), sh, ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+        nr, nz = ctypes.c_int(), ctypes.c_int()
+        te = ctypes.c_double()
+        _check("heat_info", L.heat_info(h, ctypes.byref(nr), ctypes.byref(nz), None, None, ctypes.byref(te)))
+        self.Nr, self.Nz, self.tau_exp = nr.value, nz.value, te.value
+        self.dt = float(dt)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            load().heat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def set_dt(self, dt: float):
+        _check("heat_set_dt", load().heat_set_dt(self._h, float(dt)))
+        self.dt = float(dt)
+
+    def step(self, n: int = 1):
+        _check("heat_step", load().heat_step(self._h, int(n)))
+
+    def sweep(self, direction: int):
+        """One half-step: 0 = implicit in r (to the half layer), 1 = implicit in z."""
+        _check("heat_sweep", load().heat_sweep(self._h, int(direction)))
+
+    def sync(self):
+        _check("heat_sync", load().heat_sync(self._h))
+
+    def field(self, out=None):
+        """Current temperature field.  ``out``: a CUDA float64 torch tensor of
+        Nz*Nr elements (stream-ordered copy), else a new host numpy array."""
+        n = self.Nr * self.Nz
+        if out is not None:
+            assert out.is_cuda and out.dtype.is_floating_point and out.element_size() == 8 and out.numel() == n
+            _check("heat_field", load().heat_field(self._h, ctypes.c_void_p(out.data_ptr()), n, 1))
+            return out
+        a = np.empty((self.Nz, self.Nr), dtype=np.float64)
+        _check("heat_field", load().heat_field(self._h, a.ctypes.data_as(ctypes.c_void_p), n, 0))
+        return a
+
+    def set_field(self, T):
+        n = self.Nr * self.Nz
+        if hasattr(T, "is_cuda") and T.is_cuda:
+            assert T.element_size() == 8 and T.numel() == n and T.is_contiguous()
+            _check("heat_set_field", load().heat_set_field(self._h, ctypes.c_void_p(T.data_ptr()), n, 1))
+            return
+        a = np.ascontiguousarray(T, dtype=np.float64).reshape(self.Nz, self.Nr)
+        _check("heat_set_field", load().heat_set_field(self._h, a.ctypes.data_as(ctypes.c_void_p), n, 0))
+
+    def energy(self):
+        """(E, Phi, Q) in FP64 (see include/heat.h)."""
+        e, f, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check("heat_energy", load().heat_energy(self._h, ctypes.byref(e), ctypes.byref(f), ctypes.byref(q)))
+        return e.value, f.value, q.value
+
+    def centres(self):
+        rc = np.empty(self.Nr)
+        zc = np.empty(self.Nz)
+        _check("heat_info", load().heat_info(self._h, None, None, rc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             zc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None))
+        return rc, zc
+
+    def launches_per_step(self) -> int:
+        return int(load().heat_launches_per_step(self._h))

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every symbol include/heat.h declares.
+CPU only: no compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_03744_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("heat.h")
+    assert "heat_create" in names and "heat_step" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_symbol_list_matches_header():
+    from paper_1912_03744_gb300.heat import SYMBOLS
+    assert sorted(SYMBOLS) == _declared("heat.h")
+
+
+def test_strerror_without_gpu(lib):
+    lib.heat_strerror.restype = ctypes.c_char_p
+    assert lib.heat_strerror(0) == b"ok"
+    assert lib.heat_strerror(-1) == b"invalid argument"
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    """heat_create validates on the host before touching the device."""
+    from paper_1912_03744_gb300 import heat as hb
+    hb.load()
+    L = hb._lib
+    h = ctypes.c_void_p()
+    assert L.heat_create(None, None, None, 1.0, None, ctypes.byref(h)) == -1
+    assert L.heat_step(None, 1) == -1
+    assert L.heat_sweep(None, 0) == -1
