@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-main", action="store_true",
+                    help="time the headline path only (no side-by-side, e2e or CPU legs); for profiling")
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=4096)
     args = ap.parse_args()
@@ -251,6 +253,12 @@ def main():
     _barrier(ws)
     with Clocks(local) as clk:
         main_t = time_gpu(p, args.precision, args.steps, args.warmup, flush)
+    if args.only_main:
+        tot = sum(main_t["r_ms"]) + sum(main_t["z_ms"])
+        print(json.dumps({"only_main": True, "ms_per_step": tot / args.steps,
+                          "rsweep_ms": statistics.mean(main_t["r_ms"]),
+                          "zsweep_ms": statistics.mean(main_t["z_ms"])}), flush=True)
+        return
     side_steps = max(3, min(args.steps, 200))
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)

@@ -13,6 +13,8 @@ int validate(const heat_geometry *, const heat_materials *, const heat_options *
 void build_grid(const heat_geometry *, Grid &);
 void build_tables(heat_ctx *);
 void compute_limits(heat_ctx *);
+void build_zpartition(heat_ctx *);
+cudaError_t launch_fill(heat_ctx *, int, double);
 cudaError_t launch_steps(heat_ctx *, int);
 cudaError_t launch_sweep(heat_ctx *, int);
 cudaError_t launch_energy(heat_ctx *);
@@ -74,11 +76,44 @@ int upload_tab(heat_ctx *ctx, const HostTab &T, DevTab &D)
     return HEAT_OK;
 }
 
+// Upload the packed z-partition tables in the field precision and size the
+// chunk-summary scratch.
+int upload_zpart(heat_ctx *ctx)
+{
+    ZPart &z = ctx->zp;
+    const size_t npk = ctx->zpk.size(), nch = ctx->zch.size();
+    if (ctx->precision == HEAT_FP64) {
+        if (z.pk64) cudaFree(z.pk64), z.pk64 = nullptr;
+        if (z.ch64) cudaFree(z.ch64), z.ch64 = nullptr;
+        HEAT_CHECK(cudaMalloc(&z.pk64, npk * sizeof(double)));
+        HEAT_CHECK(cudaMalloc(&z.ch64, nch * sizeof(double)));
+        HEAT_CHECK(cudaMemcpyAsync(z.pk64, ctx->zpk.data(), npk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        HEAT_CHECK(cudaMemcpyAsync(z.ch64, ctx->zch.data(), nch * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        if (!ctx->d_zsum64)
+            HEAT_CHECK(cudaMalloc(&ctx->d_zsum64, (size_t)z.n_chunks * 2 * ctx->g.Nr * sizeof(double)));
+    } else {
+        if (z.pk32) cudaFree(z.pk32), z.pk32 = nullptr;
+        if (z.ch32) cudaFree(z.ch32), z.ch32 = nullptr;
+        std::vector<float> a(ctx->zpk.begin(), ctx->zpk.end()), b(ctx->zch.begin(), ctx->zch.end());
+        HEAT_CHECK(cudaMalloc(&z.pk32, npk * sizeof(float)));
+        HEAT_CHECK(cudaMalloc(&z.ch32, nch * sizeof(float)));
+        HEAT_CHECK(cudaMemcpyAsync(z.pk32, a.data(), npk * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        HEAT_CHECK(cudaMemcpyAsync(z.ch32, b.data(), nch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        if (!ctx->d_zsum)
+            HEAT_CHECK(cudaMalloc(&ctx->d_zsum, (size_t)z.n_chunks * 2 * ctx->g.Nr * sizeof(float)));
+        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    return HEAT_OK;
+}
+
 void free_ctx(heat_ctx *ctx)
 {
     if (!ctx) return;
-    void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32, ctx->dZ.buf64, ctx->dZ.buf32, ctx->d_rowcls, ctx->d_colcls,
-                    ctx->d_wr,     ctx->d_wz,     ctx->d_field[0], ctx->d_field[1], ctx->d_part, ctx->d_res};
+    void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32,   ctx->dZ.buf64,   ctx->dZ.buf32, ctx->d_rowcls,
+                    ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
+                    ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
+                    ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -131,6 +166,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     ctx->tau = dt;
     build_grid(geom, ctx->g);
     build_tables(ctx);
+    build_zpartition(ctx);
     compute_limits(ctx);
 
     const Grid &g = ctx->g;
@@ -141,6 +177,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     };
     if ((st = upload_tab(ctx, ctx->R, ctx->dR)) != HEAT_OK) return fail(st);
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return fail(st);
+    if ((st = upload_zpart(ctx)) != HEAT_OK) return fail(st);
     std::vector<double> wr(g.Nr), wz(g.Nz);
     for (int i = 0; i < g.Nr; ++i) wr[i] = 2.0 * kPi * g.rc[i] * g.hbar[i];
     for (int j = 0; j < g.Nz; ++j) wz[j] = g.etabar[j];
@@ -156,20 +193,14 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     ctx->n_part = energy_blocks(ctx);
     HEAT_TRY(cudaMalloc(&ctx->d_part, 2 * ctx->n_part * sizeof(double)));
     HEAT_TRY(cudaMalloc(&ctx->d_res, 2 * sizeof(double)));
+    if (ctx->precision == HEAT_FP32_REFINED) HEAT_TRY(cudaMalloc(&ctx->d_rho, ncell * sizeof(float)));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_rowcls, g.rowcls.data(), g.Nz * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_colcls, g.colcls.data(), g.Nr * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_wr, wr.data(), g.Nr * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_wz, wz.data(), g.Nz * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    HEAT_TRY(cudaMemsetAsync(ctx->d_field[1], 0, ncell * elem_size(ctx), ctx->stream));
-    if (ctx->T_ref == mat->T_init) {
-        // theta = T - T_ref = 0 everywhere at T = T_init (eq. "initcond")
-        HEAT_TRY(cudaMemsetAsync(ctx->d_field[0], 0, ncell * elem_size(ctx), ctx->stream));
-    } else {
-        HEAT_TRY(cudaStreamSynchronize(ctx->stream));
-        std::vector<double> init(ncell, mat->T_init);
-        int s2 = heat_set_field(ctx, init.data(), ncell, 0);
-        if (s2 != HEAT_OK) return fail(s2);
-    }
+    // uniform initial field T = T_init (eq. "initcond"), stored as T - T_ref
+    HEAT_TRY(launch_fill(ctx, 0, mat->T_init - ctx->T_ref));
+    HEAT_TRY(launch_fill(ctx, 1, mat->T_init - ctx->T_ref));
     HEAT_TRY(cudaStreamSynchronize(ctx->stream));
 #undef HEAT_TRY
     *out = ctx;
@@ -182,9 +213,11 @@ int heat_set_dt(heat_ctx *ctx, double dt)
     HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
     ctx->tau = dt;
     build_tables(ctx);
+    build_zpartition(ctx);
     int st = upload_tab(ctx, ctx->R, ctx->dR);
     if (st != HEAT_OK) return st;
-    return upload_tab(ctx, ctx->Z, ctx->dZ);
+    if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
+    return upload_zpart(ctx);
 }
 
 int heat_sweep(heat_ctx *ctx, int dir)

@@ -69,6 +69,38 @@ struct DevTab {
     LineTab64 full{};
 };
 
+// Column partition of the z-sweep.  Every column is cut into chunks of Rc
+// rows (the last one may be shorter).  For chunk [r0, r1) of a column class
+// with factorization (inv, f, cp), and right-hand side r:
+//   forward summary   B = d'_{r1-1} with zero carry-in   = sum_j r_j wB_j,
+//                     wB_j = inv_j prod_{m=j+1}^{r1-1} f_m
+//   backward summary  G0 = x_{r0} with zero carries       = sum_j r_j wG_j,
+//                     wG_j = inv_j S_j,  S_j = C_j + f_{j+1} S_{j+1},
+//                     C_k = prod_{m=r0}^{k-1} cp_m
+//   chunk constants   F = prod_{m=r0}^{r1-1} f_m,  H = prod_{m=r0}^{r1-1} cp_m,
+//                     GP = sum_k P_k C_k,  P_k = prod_{m=r0}^{k} f_m
+// and the exact carries follow from D_c = B_c + F_c D_{c-1} (D_{-1} = 0) and
+// X_c = G0_c + GP_c D_{c-1} + H_c X_{c+1} (X_n = 0): chunk c starts its
+// forward recurrence from D_{c-1} and its backward one from X_{c+1}.
+// Packed per (class, row) table, 8 values: inv, f, cp, wB, wG, e0, e1, e2
+// with (e0, e1, e2) = (am, ap, q) for the increment form, (w, s, 0) for the
+// literal form.  Chunk constants per (class, chunk): F, H, GP (+ pad).
+struct ZPart {
+    int Rc = 0, n_chunks = 0;
+    double *pk64 = nullptr, *ch64 = nullptr;  // device
+    float *pk32 = nullptr, *ch32 = nullptr;   // device (FP32 paths)
+};
+
+// Rows per z chunk for a precision: KZ rows per thread x NW warps.
+inline int z_rows_per_thread(int precision) { return precision == HEAT_FP64 ? 8 : 16; }
+inline int z_warps(int precision, int Nz)
+{
+    const int kz = z_rows_per_thread(precision);
+    int nw = (Nz + kz - 1) / kz;
+    return nw < 1 ? 1 : (nw > 16 ? 16 : nw);
+}
+inline int z_chunk_rows(int precision, int Nz) { return z_rows_per_thread(precision) * z_warps(precision, Nz); }
+
 struct Grid {
     int Nr = 0, Nz = 0;
     double r_lo = 0, r_hi = 0, z_lo = 0, z_hi = 0;
@@ -95,6 +127,11 @@ struct heat_ctx {
     double tau = 0.0, tau_exp = 0.0;
     double E_ref = 0.0, Q = 0.0;  // 2 pi sum C T_ref r hbar etabar; source power
     heat::HostTab R, Z;
+    std::vector<double> zpk, zch;  // host z-partition tables (see ZPart)
+    heat::ZPart zp;
+    float *d_zsum = nullptr;       // z-sweep chunk summaries (scratch), FP32 paths
+    double *d_zsum64 = nullptr;    // z-sweep chunk summaries (scratch), FP64 path
+    float *d_rho = nullptr;        // refined path: FP32 residual field (scratch)
     // device
     heat::DevTab dR, dZ;
     int *d_rowcls = nullptr, *d_colcls = nullptr;

@@ -48,9 +48,9 @@ int validate(const heat_geometry *g, const heat_materials *mt, const heat_option
         if (!(g->z_faces[l + 1] > g->z_faces[l]) || g->z_cells[l] < 1) return HEAT_ERR_ARG;
         Nz += g->z_cells[l];
     }
-    // r-lines are solved by one block of <= 1024 threads x <= 32 cells; z-lines
-    // by one cluster of <= 16 blocks x 32 warps x 32 rows
-    if (Nr > 32768 || Nz > 16384 || Nr * Nz > (1LL << 34)) return HEAT_ERR_ARG;
+    // r-lines are solved by one block of <= 1024 threads x <= 32 cells; the
+    // z-sweep keeps one carry per column chunk in shared memory (<= 512 chunks)
+    if (Nr > 32768 || Nz > 65536 || Nr * Nz > (1LL << 34)) return HEAT_ERR_ARG;
     for (int f = 0; f < 4; ++f)
         if ((g->bc[f] != HEAT_BC_NEUMANN && g->bc[f] != HEAT_BC_DIRICHLET) || !std::isfinite(g->T_bc[f]))
             return HEAT_ERR_ARG;
@@ -232,6 +232,66 @@ void build_tables(heat_ctx *ctx)
         for (int j = 0; j < Nz; ++j) reg[j] = first_region(g.colmask[b] & g.maskZ[j], ctx->box_region);
         fill_class(ctx->Z, b, reg, ones_c, ones_c, g.eta, g.etabar, g.dz, ctx->bc[2], ctx->bc[3], ctx->theta_bc[2],
                    ctx->theta_bc[3], ctx, tau);
+    }
+}
+
+// Packed z-sweep tables and chunk constants for the column partition (see
+// ZPart in heat_internal.h); FP64 on the host.
+void build_zpartition(heat_ctx *ctx)
+{
+    const HostTab &Z = ctx->Z;
+    const int Nz = Z.N, nb = Z.n_class;
+    const int Rc = z_chunk_rows(ctx->precision, Nz);
+    const int nch = (Nz + Rc - 1) / Rc;
+    ctx->zp.Rc = Rc;
+    ctx->zp.n_chunks = nch;
+    ctx->zpk.assign((size_t)nb * Nz * 8, 0.0);
+    ctx->zch.assign((size_t)nb * nch * 4, 0.0);
+    const bool lit = ctx->precision == HEAT_FP64;
+    std::vector<double> C(Rc + 1), P(Rc), S(Rc + 1);
+    for (int b = 0; b < nb; ++b) {
+        const size_t o = (size_t)b * Nz;
+        for (int c = 0; c < nch; ++c) {
+            const int r0 = c * Rc, r1 = std::min(Nz, r0 + Rc), n = r1 - r0;
+            // C_k = prod_{m=r0}^{k-1} cp_m, P_k = prod_{m=r0}^{k} f_m (local index k - r0)
+            C[0] = 1.0;
+            for (int k = 0; k < n; ++k) C[k + 1] = C[k] * Z.cp[o + r0 + k];
+            double pp = 1.0;
+            for (int k = 0; k < n; ++k) {
+                pp *= Z.f[o + r0 + k];
+                P[k] = pp;
+            }
+            // wB_j = inv_j prod_{m=j+1}^{r1-1} f_m
+            double tail = 1.0;
+            for (int k = n - 1; k >= 0; --k) {
+                double *e = &ctx->zpk[(o + r0 + k) * 8];
+                e[3] = Z.inv[o + r0 + k] * tail;
+                tail *= Z.f[o + r0 + k];
+            }
+            // S_j = C_j + f_{j+1} S_{j+1}, wG_j = inv_j S_j
+            S[n] = 0.0;
+            for (int k = n - 1; k >= 0; --k) {
+                const double fn = k + 1 < n ? Z.f[o + r0 + k + 1] : 0.0;
+                S[k] = C[k] + fn * S[k + 1];
+                ctx->zpk[(o + r0 + k) * 8 + 4] = Z.inv[o + r0 + k] * S[k];
+            }
+            double gp = 0.0;
+            for (int k = 0; k < n; ++k) gp += P[k] * C[k];
+            double *ch = &ctx->zch[((size_t)b * nch + c) * 4];
+            ch[0] = P[n - 1];
+            ch[1] = C[n];
+            ch[2] = gp;
+            ch[3] = 0.0;
+        }
+        for (int j = 0; j < Nz; ++j) {
+            double *e = &ctx->zpk[(o + j) * 8];
+            e[0] = Z.inv[o + j];
+            e[1] = Z.f[o + j];
+            e[2] = Z.cp[o + j];
+            e[5] = lit ? Z.w[o + j] : Z.am[o + j];
+            e[6] = lit ? Z.s[o + j] : Z.ap[o + j];
+            e[7] = lit ? 0.0 : Z.q[o + j];
+        }
     }
 }
 

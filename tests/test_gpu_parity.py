@@ -12,7 +12,7 @@ from workloads import heat as H
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32_refined": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,7 +48,7 @@ def _run_pair(p, steps, precision, T0=None, factor=H.DT_FACTOR):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refined"])
 def test_config1_full_run(precision):
     """64x128 five-region cell, 200 steps at dt = 50 tau_exp."""
     p = H.config1()
@@ -69,7 +69,7 @@ def test_grid_and_limit_parity():
         s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refined"])
 def test_half_step_parity(precision):
     """The half layer Tbar (eq. scheme_eq_1) and the full step separately."""
     p = H.config2(96, 200)
@@ -87,8 +87,8 @@ def test_half_step_parity(precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("shape", [(256, 512), (333, 517), (1000, 130)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refined"])
+@pytest.mark.parametrize("shape", [(256, 512), (333, 517), (1000, 130), (64, 3000)])
 def test_config2_reduced_grids(precision, shape):
     """Config 2's seeded problem on reduced (and ragged) grids, 60 steps."""
     p = H.config2(*shape)
@@ -197,10 +197,29 @@ def test_device_field_roundtrip():
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refined"])
 def test_full_size_config2_few_steps(precision):
     """Config 2 at its full 2048 x 4096 size, in the launch configuration the
     benchmark times, 3 steps against the oracle on the whole field."""
     p = H.config2()
     Tg, To = _run_pair(p, 3, precision)
     assert _rel(Tg, To) <= TOL[precision]
+
+
+def test_refined_path_is_more_accurate_at_high_contrast():
+    """Config 4's 1e4 conductivity contrast on a 512 x 1024 grid, 50 steps:
+    the FP64-residual refined FP32 path is at least as close to the oracle
+    as the plain FP32 path, and both meet the FP32 bar."""
+    p = H.config4(512, 1024)
+    o = Oracle(p)
+    tau = H.DT_FACTOR * o.tau_exp()
+    o.step(tau, 50)
+    To = o.field()
+    errs = {}
+    for prec in ("fp32", "fp32_refined"):
+        s = _solver(p, tau, prec)
+        s.step(50)
+        errs[prec] = _rel(s.field(), To)
+        s.close()
+    assert errs["fp32_refined"] <= errs["fp32"] * 1.01, errs
+    assert max(errs.values()) <= 1e-5, errs
