@@ -41,26 +41,27 @@ int cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_); \
     } while (0)
 
-constexpr int kFields64 = 18;
-constexpr int kFields32 = 12;
+constexpr int kFields64 = 20;
+constexpr int kFields32 = 14;
 
-// Upload one direction's host tables: FP64 master (18 fields) and, for the
-// FP32 paths, an FP32 copy of the 12 fields the sweeps use.
+// Upload one direction's host tables: FP64 master (20 fields) and, for the
+// FP32 paths, an FP32 copy of the 14 fields the sweeps use.
 int upload_tab(heat_ctx *ctx, const HostTab &T, DevTab &D)
 {
     const size_t n = (size_t)T.n_class * T.N;
     if (!D.buf64) HEAT_CHECK(cudaMalloc(&D.buf64, kFields64 * n * sizeof(double)));
-    const std::vector<double> *src[kFields64] = {&T.inv, &T.f,  &T.cp, &T.w,  &T.s, &T.am,  &T.ap,   &T.ad,  &T.sd,
-                                                 &T.dl,  &T.dh, &T.q,  &T.m,  &T.b, &T.p,   &T.cap, &T.dsum, &T.dbc};
+    const std::vector<double> *src[kFields64] = {&T.inv, &T.f, &T.cp, &T.w,  &T.s,  &T.am, &T.ap,
+                                                 &T.ad,  &T.sd, &T.dl, &T.dh, &T.q,  &T.xm, &T.xp,
+                                                 &T.m,   &T.b,  &T.p,  &T.cap, &T.dsum, &T.dbc};
     std::vector<double> host(kFields64 * n);
     for (int a = 0; a < kFields64; ++a) std::memcpy(host.data() + a * n, src[a]->data(), n * sizeof(double));
     HEAT_CHECK(cudaMemcpyAsync(D.buf64, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
                                ctx->stream));
     double *p = D.buf64;
     auto F = [&](int a) { return (const double *)(p + a * n); };
-    D.t64 = LineTab<double>{F(0), F(1), F(2), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11)};
-    D.full = LineTab64{F(12), F(13), F(14), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11),
-                       F(15), F(16), F(17)};
+    D.t64 = LineTab<double>{F(0), F(1), F(2), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11), F(12), F(13)};
+    D.full = LineTab64{F(14), F(15), F(16), F(3), F(4), F(5), F(6), F(7), F(8), F(9), F(10), F(11),
+                       F(17), F(18), F(19)};
     if (ctx->precision != HEAT_FP64) {
         if (!D.buf32) HEAT_CHECK(cudaMalloc(&D.buf32, kFields32 * n * sizeof(float)));
         std::vector<float> h32(kFields32 * n);
@@ -69,41 +70,50 @@ int upload_tab(heat_ctx *ctx, const HostTab &T, DevTab &D)
                                    ctx->stream));
         float *q = D.buf32;
         auto G = [&](int a) { return (const float *)(q + a * n); };
-        D.t32 = LineTab<float>{G(0), G(1), G(2), G(3), G(4), G(5), G(6), G(7), G(8), G(9), G(10), G(11)};
+        D.t32 = LineTab<float>{G(0), G(1), G(2), G(3), G(4), G(5), G(6), G(7), G(8), G(9), G(10), G(11), G(12), G(13)};
     }
     // host vectors are freed on return: the copies must complete first
     HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
     return HEAT_OK;
 }
 
-// Upload the packed z-partition tables in the field precision and size the
-// chunk-summary scratch.
+// Upload the packed z-partition tables in the field precision, laid out as
+// [pkA: 4 per (class,row)][pkB: 4], plus the chunk constants, and size the
+// chunk scratch (summaries, then carries: 2 x n_chunks x Nr).
+template <typename real>
+int upload_zpart_t(heat_ctx *ctx, real *&pk, real *&ch)
+{
+    const size_t npk = (size_t)ctx->Z.n_class * ctx->Z.N;
+    std::vector<real> h(8 * npk);
+    for (size_t e = 0; e < npk; ++e) {
+        const double *src = &ctx->zpk[e * 8];
+        for (int f = 0; f < 4; ++f) h[e * 4 + f] = (real)src[f];
+        for (int f = 0; f < 4; ++f) h[4 * npk + e * 4 + f] = (real)src[4 + f];
+    }
+    std::vector<real> hc(ctx->zch.begin(), ctx->zch.end());
+    if (pk) cudaFree(pk), pk = nullptr;
+    if (ch) cudaFree(ch), ch = nullptr;
+    HEAT_CHECK(cudaMalloc(&pk, h.size() * sizeof(real)));
+    HEAT_CHECK(cudaMalloc(&ch, hc.size() * sizeof(real)));
+    HEAT_CHECK(cudaMemcpyAsync(pk, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_CHECK(cudaMemcpyAsync(ch, hc.data(), hc.size() * sizeof(real), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    return HEAT_OK;
+}
+
 int upload_zpart(heat_ctx *ctx)
 {
     ZPart &z = ctx->zp;
-    const size_t npk = ctx->zpk.size(), nch = ctx->zch.size();
+    const size_t nsum = (size_t)z.n_chunks * 4 * ctx->g.Nr;  // summaries [nch][2][Nr] + carries [nch][2][Nr]
     if (ctx->precision == HEAT_FP64) {
-        if (z.pk64) cudaFree(z.pk64), z.pk64 = nullptr;
-        if (z.ch64) cudaFree(z.ch64), z.ch64 = nullptr;
-        HEAT_CHECK(cudaMalloc(&z.pk64, npk * sizeof(double)));
-        HEAT_CHECK(cudaMalloc(&z.ch64, nch * sizeof(double)));
-        HEAT_CHECK(cudaMemcpyAsync(z.pk64, ctx->zpk.data(), npk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        HEAT_CHECK(cudaMemcpyAsync(z.ch64, ctx->zch.data(), nch * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        if (!ctx->d_zsum64)
-            HEAT_CHECK(cudaMalloc(&ctx->d_zsum64, (size_t)z.n_chunks * 2 * ctx->g.Nr * sizeof(double)));
+        int st = upload_zpart_t<double>(ctx, z.pk64, z.ch64);
+        if (st != HEAT_OK) return st;
+        if (!ctx->d_zsum64) HEAT_CHECK(cudaMalloc(&ctx->d_zsum64, nsum * sizeof(double)));
     } else {
-        if (z.pk32) cudaFree(z.pk32), z.pk32 = nullptr;
-        if (z.ch32) cudaFree(z.ch32), z.ch32 = nullptr;
-        std::vector<float> a(ctx->zpk.begin(), ctx->zpk.end()), b(ctx->zch.begin(), ctx->zch.end());
-        HEAT_CHECK(cudaMalloc(&z.pk32, npk * sizeof(float)));
-        HEAT_CHECK(cudaMalloc(&z.ch32, nch * sizeof(float)));
-        HEAT_CHECK(cudaMemcpyAsync(z.pk32, a.data(), npk * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-        HEAT_CHECK(cudaMemcpyAsync(z.ch32, b.data(), nch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-        if (!ctx->d_zsum)
-            HEAT_CHECK(cudaMalloc(&ctx->d_zsum, (size_t)z.n_chunks * 2 * ctx->g.Nr * sizeof(float)));
-        HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+        int st = upload_zpart_t<float>(ctx, z.pk32, z.ch32);
+        if (st != HEAT_OK) return st;
+        if (!ctx->d_zsum) HEAT_CHECK(cudaMalloc(&ctx->d_zsum, nsum * sizeof(float)));
     }
-    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
     return HEAT_OK;
 }
 

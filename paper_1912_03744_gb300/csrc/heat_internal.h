@@ -38,13 +38,17 @@ constexpr double kPi = 3.14159265358979323846;
 //                (ad = -(m + p + D), sd = D theta_bc).
 //   dl, dh, q  : Dirichlet coefficient of the low / high outer face (0 off the
 //                face) and the volumetric source (0 on void), used by the
-//                increment form (see heat_sweeps.cu).
+//                increment form.
+//   xm, xp     : the couplings of the increment form with each outer
+//                Dirichlet face folded in: at the first cell xm = D_lo (the
+//                ghost neighbour then holds theta_bc), at the last cell
+//                xp = D_hi; elsewhere xm = am, xp = ap.
 //   m, b, p    : the matrix itself (FP64 only; residuals of the refined path).
 //   cap, dsum, dbc : FP64 energy/flux weights: C (0 on void), sum of the
 //                Dirichlet coefficients D of this direction and D theta_bc.
 template <typename real>
 struct LineTab {
-    const real *inv, *f, *cp, *w, *s, *am, *ap, *ad, *sd, *dl, *dh, *q;
+    const real *inv, *f, *cp, *w, *s, *am, *ap, *ad, *sd, *dl, *dh, *q, *xm, *xp;
 };
 
 struct LineTab64 {
@@ -55,23 +59,23 @@ struct LineTab64 {
 // Host FP64 master of one direction's tables.
 struct HostTab {
     int n_class = 0, N = 0;
-    std::vector<double> inv, f, cp, w, s, am, ap, ad, sd, dl, dh, q, m, b, p, cap, dsum, dbc;
+    std::vector<double> inv, f, cp, w, s, am, ap, ad, sd, dl, dh, q, xm, xp, m, b, p, cap, dsum, dbc;
     std::vector<double> ssum;  // sum of all couplings (for tau_exp)
     void resize(int nc, int n);
 };
 
 // Device copy of one direction's tables (FP64 always; FP32 copy when needed).
 struct DevTab {
-    double *buf64 = nullptr;  // 18 fields x n_class x N doubles
-    float *buf32 = nullptr;   // 12 fields x n_class x N floats
+    double *buf64 = nullptr;  // 20 fields x n_class x N doubles
+    float *buf32 = nullptr;   // 14 fields x n_class x N floats
     LineTab<double> t64{};
     LineTab<float> t32{};
     LineTab64 full{};
 };
 
 // Column partition of the z-sweep.  Every column is cut into chunks of Rc
-// rows (the last one may be shorter).  For chunk [r0, r1) of a column class
-// with factorization (inv, f, cp), and right-hand side r:
+// rows (the last one may be shorter).  For a chunk [r0, r1) of a column class
+// with factorization (inv, f, cp) and right-hand side r:
 //   forward summary   B = d'_{r1-1} with zero carry-in   = sum_j r_j wB_j,
 //                     wB_j = inv_j prod_{m=j+1}^{r1-1} f_m
 //   backward summary  G0 = x_{r0} with zero carries       = sum_j r_j wG_j,
@@ -82,24 +86,26 @@ struct DevTab {
 // and the exact carries follow from D_c = B_c + F_c D_{c-1} (D_{-1} = 0) and
 // X_c = G0_c + GP_c D_{c-1} + H_c X_{c+1} (X_n = 0): chunk c starts its
 // forward recurrence from D_{c-1} and its backward one from X_{c+1}.
-// Packed per (class, row) table, 8 values: inv, f, cp, wB, wG, e0, e1, e2
-// with (e0, e1, e2) = (am, ap, q) for the increment form, (w, s, 0) for the
-// literal form.  Chunk constants per (class, chunk): F, H, GP (+ pad).
+// Packed per (class, row) tables, 8 values: pkA = {inv, f, cp, e0},
+// pkB = {e1, e2, wB, wG} with (e0, e1, e2) = (q, xm, xp) for the increment
+// form, (s, w, 0) for the literal form.  Per (class, chunk): {F, H, GP, 0}.
 struct ZPart {
     int Rc = 0, n_chunks = 0;
     double *pk64 = nullptr, *ch64 = nullptr;  // device
     float *pk32 = nullptr, *ch32 = nullptr;   // device (FP32 paths)
 };
 
-// Rows per z chunk for a precision: KZ rows per thread x NW warps.
-inline int z_rows_per_thread(int precision) { return precision == HEAT_FP64 ? 8 : 16; }
-inline int z_warps(int precision, int Nz)
+// Rows per z chunk (one warp walks a chunk of its columns): 32, or more
+// (a multiple of 4) so that a column has at most 256 chunks.
+inline int z_chunk_rows(int, int Nz)
 {
-    const int kz = z_rows_per_thread(precision);
-    int nw = (Nz + kz - 1) / kz;
-    return nw < 1 ? 1 : (nw > 16 ? 16 : nw);
+    if (Nz <= 32) return Nz;
+    int rc = (Nz + 255) / 256;
+    rc = (rc + 3) / 4 * 4;
+    return rc < 32 ? 32 : rc;
 }
-inline int z_chunk_rows(int precision, int Nz) { return z_rows_per_thread(precision) * z_warps(precision, Nz); }
+// Columns per thread of the z-sweep (one 8- or 16-byte row segment).
+inline int z_cols_per_thread(int) { return 2; }
 
 struct Grid {
     int Nr = 0, Nz = 0;
@@ -127,10 +133,10 @@ struct heat_ctx {
     double tau = 0.0, tau_exp = 0.0;
     double E_ref = 0.0, Q = 0.0;  // 2 pi sum C T_ref r hbar etabar; source power
     heat::HostTab R, Z;
-    std::vector<double> zpk, zch;  // host z-partition tables (see ZPart)
+    std::vector<double> zpk, zch;  // host z-partition tables (see ZPart): 8 per (class,row)
     heat::ZPart zp;
-    float *d_zsum = nullptr;       // z-sweep chunk summaries (scratch), FP32 paths
-    double *d_zsum64 = nullptr;    // z-sweep chunk summaries (scratch), FP64 path
+    float *d_zsum = nullptr;       // z-sweep chunk summaries then carries (scratch), FP32 paths
+    double *d_zsum64 = nullptr;    // z-sweep chunk summaries then carries (scratch), FP64 path
     float *d_rho = nullptr;        // refined path: FP32 residual field (scratch)
     // device
     heat::DevTab dR, dZ;

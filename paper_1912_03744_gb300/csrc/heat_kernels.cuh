@@ -488,357 +488,509 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const rea
 }
 
 // ------------------------------------------------------------------ z-sweep
-// Right-hand side of the z-line system at (i, j) for a lane, given the column
-// values tm, t, tp (rows j-1, j, j+1) and the row neighbours tl, tr.
-template <typename real, int MODE>
-__device__ __forceinline__ real z_rhs(real tm, real t, real tp, real tl, real tr, real e0, real e1, real e2, real ra,
-                                      real rb, real rc, real rd, real zdl, real zdh, const real (&bcv)[4])
-{
-    if constexpr (MODE == MODE_LIT) {
-        // e0 = w, e1 = s; ra, rb, rc, rd = R.am, R.ap, R.ad, R.sd
-        return fmad(e0 + rc, t, fmad(ra, tl, fmad(rb, tr, e1 + rd)));
-    } else {
-        // e0 = Z.am, e1 = Z.ap, e2 = q; ra, rb, rc, rd = R.am, R.ap, R.dl, R.dh
-        real r = e2;
-        r = fmad(e0, tm - t, r);
-        r = fmad(e1, tp - t, r);
-        r = fmad(ra, tl - t, r);
-        r = fmad(rb, tr - t, r);
-        r = fmad(rc, bcv[0] - t, r);
-        r = fmad(rd, bcv[1] - t, r);
-        r = fmad(zdl, bcv[2] - t, r);
-        r = fmad(zdh, bcv[3] - t, r);
-        return r;
-    }
-}
+// Interleaved Thomas inside column chunks.  A warp owns 32*V adjacent columns
+// (V per lane: one 16-byte segment of a row, so every row access of the warp
+// is one contiguous run) and one chunk of Rc rows; each lane walks its chunk
+// row by row.  Pass 1 (zsum) reduces every (column, chunk) to its two carry
+// summaries; pass 2 (zcarry) runs the carry recurrences of each column over
+// its chunks; pass 3 (zsolve) walks each chunk forward from its carry
+// (forward results in shared memory) and back from its other carry, writing
+// the new field.  In the increment form every outer Dirichlet face is folded
+// into the coupling of the boundary cell (xm, xp tables) and the ghost
+// neighbour holds theta_bc, so the right-hand side needs no boundary branch.
 
-template <typename real>
-__device__ __forceinline__ void ld_pack(const real *p, real (&e)[8])
-{
-    if constexpr (sizeof(real) == 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(p + 4));
-        e[0] = a.x, e[1] = a.y, e[2] = a.z, e[3] = a.w, e[4] = b.x, e[5] = b.y, e[6] = b.z, e[7] = b.w;
-    } else {
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            const double2 a = __ldg(reinterpret_cast<const double2 *>(p + q));
-            e[q] = a.x, e[q + 1] = a.y;
-        }
+template <typename real, int V>
+struct VecIO;
+template <>
+struct VecIO<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float (&v)[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
     }
-}
-
-// Per-thread context of the z kernels: the thread's column, rows and the
-// right-hand side of its rows (computed from the field, or read from rho).
-template <typename real, int KZ>
-struct ZThread {
-    int i, j0, j1, b;
-    bool col;
-    real d[KZ];
-    real t[KZ];
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct VecIO<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double (&v)[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x, v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&v)[2])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
 };
 
-template <typename real, int KZ, int MODE>
-__device__ __forceinline__ void z_load_rhs(ZThread<real, KZ> &T, const real *__restrict__ th,
-                                           const real *__restrict__ rho, int Nr, int Nz,
-                                           const int *__restrict__ rowcls, const real *__restrict__ pkb,
-                                           LineTab<real> R, LineTab<real> Z, const real (&bcv)[4], int lane)
+// Four consecutive reals (aligned) from a read-only table.
+template <typename real>
+__device__ __forceinline__ void ld4(const real *p, real (&e)[4])
 {
-    const int i = T.i;
-    const bool col = T.col;
-    if constexpr (MODE == MODE_CORR) {
-#pragma unroll
-        for (int k = 0; k < KZ; ++k) {
-            const int j = T.j0 + k;
-            T.d[k] = (col && j < T.j1) ? rho[(size_t)j * Nr + i] : real(0);
-            T.t[k] = real(0);
-        }
-        return;
-    }
-    int acur = -1;
-    real ra = real(0), rb = real(0), rc = real(0), rd = real(0);
-    real tprev = (col && T.j0 - 1 >= 0 && T.j0 - 1 < Nz) ? th[(size_t)(T.j0 - 1) * Nr + i] : real(0);
-    real tcur = (col && T.j0 < Nz) ? th[(size_t)T.j0 * Nr + i] : real(0);
-#pragma unroll
-    for (int k = 0; k < KZ; ++k) {
-        const int j = T.j0 + k;
-        const bool vr = j < T.j1;
-        const real tnext = (col && j + 1 < Nz) ? th[(size_t)(j + 1) * Nr + i] : real(0);
-        const int a = vr ? rowcls[j] : acur;
-        if (a != acur && vr) {
-            if (col) {
-                const size_t ro = (size_t)a * Nr + i;
-                ra = R.am[ro];
-                rb = R.ap[ro];
-                if constexpr (MODE == MODE_LIT) {
-                    rc = R.ad[ro];
-                    rd = R.sd[ro];
-                } else {
-                    rc = R.dl[ro];
-                    rd = R.dh[ro];
-                }
-            }
-            acur = a;
-        }
-        real tl = __shfl_up_sync(HEAT_FULL_MASK, tcur, 1);
-        real tr = __shfl_down_sync(HEAT_FULL_MASK, tcur, 1);
-        if (lane == 0) tl = (col && i > 0 && vr) ? th[(size_t)j * Nr + i - 1] : tcur;
-        if (lane == 31) tr = (i + 1 < Nr && vr) ? th[(size_t)j * Nr + i + 1] : tcur;
-        real dd = real(0);
-        if (col && vr) {
-            real e[8];
-            ld_pack(pkb + (size_t)j * 8, e);
-            real zdl = real(0), zdh = real(0);
-            if (MODE != MODE_LIT && (j == 0 || j == Nz - 1)) {
-                zdl = Z.dl[(size_t)T.b * Nz + j];
-                zdh = Z.dh[(size_t)T.b * Nz + j];
-            }
-            dd = z_rhs<real, MODE>(tprev, tcur, tnext, tl, tr, e[5], e[6], e[7], ra, rb, rc, rd, zdl, zdh, bcv);
-        }
-        T.d[k] = dd;
-        T.t[k] = tcur;
-        tprev = tcur;
-        tcur = tnext;
+    if constexpr (sizeof(real) == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        e[0] = t.x, e[1] = t.y, e[2] = t.z, e[3] = t.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+        e[0] = a.x, e[1] = a.y, e[2] = b.x, e[3] = b.y;
     }
 }
 
-// Pass 1: chunk summaries B = sum r wB, G0 = sum r wG per column.
-// Grid (strips, chunks); block 32 x NW; summaries written to zsum[c][0|1][i].
-template <typename real, int KZ, int MODE>
-__global__ void __launch_bounds__(512, 2) zsum_kernel(const real *__restrict__ th, const real *__restrict__ rho, int Nr,
+// Per-lane state of the z kernels, everything loop-invariant hoisted.
+template <typename real, int V, int MODE>
+struct ZLane {
+    static constexpr bool LIT = MODE == MODE_LIT;
+    const real *th;          // field base
+    int Nr, Nz, ib, lane;
+    bool any, vec, uni, lo_edge, hi_edge;
+    int b[V];
+    const real *pa[V], *pb[V];  // packed table rows of each column's class at row 0
+    int acur;
+    real ra[V], rb[V], rc[V], rd[V];  // increment: xm, xp; literal: am, ap, ad, sd
+    real bz_lo, bz_hi, br_lo, br_hi;   // ghost values beyond the outer faces
+
+    __device__ __forceinline__ void init(const real *th_, const int *__restrict__ colcls, const real *__restrict__ pkA,
+                                         const real *__restrict__ pkB, int Nr_, int Nz_, int ib_, int lane_,
+                                         const BcVals &bc)
+    {
+        th = th_, Nr = Nr_, Nz = Nz_, ib = ib_, lane = lane_;
+        any = ib < Nr;
+        vec = (Nr % V) == 0;
+        lo_edge = ib == 0;
+        hi_edge = ib < Nr && ib + V >= Nr;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            b[q] = ib + q < Nr ? colcls[ib + q] : (any ? colcls[ib] : 0);
+            pa[q] = pkA + (size_t)b[q] * Nz * 4;
+            pb[q] = pkB + (size_t)b[q] * Nz * 4;
+        }
+        uni = true;
+#pragma unroll
+        for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
+        acur = -1;
+#pragma unroll
+        for (int q = 0; q < V; ++q) ra[q] = rb[q] = rc[q] = rd[q] = real(0);
+        // the literal form has zero couplings on the outer faces; the ghost
+        // value then only has to be finite
+        bz_lo = LIT ? real(0) : (real)bc.th[2];
+        bz_hi = LIT ? real(0) : (real)bc.th[3];
+        br_lo = LIT ? real(0) : (real)bc.th[0];
+        br_hi = LIT ? real(0) : (real)bc.th[1];
+    }
+    __device__ __forceinline__ void row_class(int a, const LineTab<real> &R)
+    {
+        if (a == acur) return;
+        acur = a;
+        const size_t ro = (size_t)a * Nr;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int i = ib + q;
+            const bool in = i < Nr;
+            if constexpr (LIT) {
+                ra[q] = in ? R.am[ro + i] : real(0);
+                rb[q] = in ? R.ap[ro + i] : real(0);
+                rc[q] = in ? R.ad[ro + i] : real(0);
+                rd[q] = in ? R.sd[ro + i] : real(0);
+            } else {
+                ra[q] = in ? R.xm[ro + i] : real(0);
+                rb[q] = in ? R.xp[ro + i] : real(0);
+            }
+        }
+    }
+    // row j of the lane's columns; ghost rows hold theta_bc
+    __device__ __forceinline__ void row(const real *__restrict__ src, int j, real (&v)[V]) const
+    {
+        if (j < 0 || j >= Nz) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = j < 0 ? bz_lo : bz_hi;
+            return;
+        }
+        const real *p = src + (size_t)j * Nr + ib;
+        if (vec) {
+            if (any) VecIO<real, V>::ld(p, v);
+            else
+#pragma unroll
+                for (int q = 0; q < V; ++q) v[q] = real(0);
+        } else {
+            // columns past the field sit right of the last column: they hold
+            // its ghost value, which its folded coupling xp multiplies
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : br_hi;
+        }
+    }
+    // left / right neighbours of the lane's first / last column in row j
+    __device__ __forceinline__ void halo(int j, const real (&t)[V], real &tl, real &tr) const
+    {
+        tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
+        tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
+        if (lane == 0 && ib > 0 && ib - 1 < Nr) tl = th[(size_t)j * Nr + ib - 1];
+        if (lane == 31 && ib + V < Nr) tr = th[(size_t)j * Nr + ib + V];
+        if (lo_edge) tl = br_lo;
+        if (hi_edge) tr = br_hi;
+    }
+    // packed table entries of row j for column q
+    __device__ __forceinline__ void tables(int j, real (&eA)[V][4], real (&eB)[V][4]) const
+    {
+        ld4<real>(pa[0] + 4 * j, eA[0]);
+        ld4<real>(pb[0] + 4 * j, eB[0]);
+#pragma unroll
+        for (int q = 1; q < V; ++q) {
+            if (uni) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) eA[q][u] = eA[0][u], eB[q][u] = eB[0][u];
+            } else {
+                ld4<real>(pa[q] + 4 * j, eA[q]);
+                ld4<real>(pb[q] + 4 * j, eB[q]);
+            }
+        }
+    }
+    // right-hand side of row j from rows j-1, j, j+1 and the row neighbours
+    __device__ __forceinline__ void rhs(const real (&tm)[V], const real (&t)[V], const real (&tp)[V], real tl, real tr,
+                                        const real (&eA)[V][4], const real (&eB)[V][4], real (&d)[V]) const
+    {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const real x = t[q];
+            const real l = q > 0 ? t[q - 1] : tl;
+            const real r = q < V - 1 ? t[q + 1] : tr;
+            if constexpr (LIT) {
+                // eA[3] = s, eB[0] = w
+                d[q] = fmad(eB[q][0] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, eA[q][3] + rd[q])));
+            } else {
+                // eA[3] = q, eB[0] = xm (z), eB[1] = xp (z)
+                real v = fmad(eB[q][0], tm[q] - x, eA[q][3]);
+                v = fmad(eB[q][1], tp[q] - x, v);
+                v = fmad(ra[q], l - x, v);
+                d[q] = fmad(rb[q], r - x, v);
+            }
+        }
+    }
+};
+
+// Walks rows [j0, j1), computing each row's right-hand side (or reading rho)
+// and calling emit(j, d, eA, eB).  Rows are loaded ZP at a time (field rows,
+// halo values and table rows of the whole group issued together) so that a
+// lane has ZP rows of loads in flight.
+constexpr int ZP = 4;
+
+template <typename real, int V, int MODE, typename Emit>
+__device__ __forceinline__ void z_walk(ZLane<real, V, MODE> &L, const real *__restrict__ rho, int j0, int j1,
+                                       const int *__restrict__ rowcls, const LineTab<real> &R, Emit emit)
+{
+    real tm[V], t[V];
+    if constexpr (MODE != MODE_CORR) {
+        L.row(L.th, j0 - 1, tm);
+        L.row(L.th, j0, t);
+    }
+    for (int jb = j0; jb < j1; jb += ZP) {
+        real nx[ZP][V], eA[ZP][V][4], eB[ZP][V][4], hl[ZP], hr[ZP];
+        int cls[ZP];
+#pragma unroll
+        for (int p = 0; p < ZP; ++p) {
+            const int j = jb + p;
+            const int jj = j < j1 ? j : j1 - 1;
+            L.tables(jj, eA[p], eB[p]);
+            if constexpr (MODE == MODE_CORR) {
+                L.row(rho, jj, nx[p]);
+            } else {
+                L.row(L.th, j + 1, nx[p]);
+                cls[p] = rowcls[jj];
+                hl[p] = (L.lane == 0 && L.ib > 0 && L.ib - 1 < L.Nr) ? L.th[(size_t)jj * L.Nr + L.ib - 1] : real(0);
+                hr[p] = (L.lane == 31 && L.ib + V < L.Nr) ? L.th[(size_t)jj * L.Nr + L.ib + V] : real(0);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < ZP; ++p) {
+            const int j = jb + p;
+            if (j >= j1) break;
+            real d[V];
+            if constexpr (MODE == MODE_CORR) {
+#pragma unroll
+                for (int q = 0; q < V; ++q) d[q] = nx[p][q];
+            } else {
+                real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
+                real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
+                if (L.lane == 0 && L.ib > 0) tl = hl[p];
+                if (L.lane == 31 && L.ib + V < L.Nr) tr = hr[p];
+                if (L.lo_edge) tl = L.br_lo;
+                if (L.hi_edge) tr = L.br_hi;
+                L.row_class(cls[p], R);
+                L.rhs(tm, t, nx[p], tl, tr, eA[p], eB[p], d);
+#pragma unroll
+                for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = nx[p][q];
+            }
+            emit(j, d, eA[p], eB[p]);
+        }
+    }
+}
+
+// Pass 1: summaries B = sum r wB and G0 = sum r wG of every (column, chunk):
+// zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks).
+template <typename real, int V, int MODE>
+__global__ void __launch_bounds__(128) zsum_kernel(const real *__restrict__ th, const real *__restrict__ rho, int Nr,
                                                    int Nz, int Rc, const int *__restrict__ rowcls,
-                                                   const int *__restrict__ colcls, const real *__restrict__ pk,
-                                                   LineTab<real> R, LineTab<real> Z, BcVals bc,
-                                                   real *__restrict__ zsum)
+                                                   const int *__restrict__ colcls, const real *__restrict__ pkA,
+                                                   const real *__restrict__ pkB, LineTab<real> R, BcVals bc,
+                                                   real *__restrict__ zs)
 {
-    __shared__ real sBs[16][33], sGs[16][33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
     const int c = blockIdx.y;
-    ZThread<real, KZ> T;
-    T.i = blockIdx.x * 32 + lane;
-    T.col = T.i < Nr;
-    T.b = T.col ? colcls[T.i] : 0;
-    const int r0 = c * Rc, r1 = min(Nz, r0 + Rc);
-    T.j0 = min(r0 + w * KZ, r1);
-    T.j1 = min(T.j0 + KZ, r1);
-    const real bcv[4] = {(real)bc.th[0], (real)bc.th[1], (real)bc.th[2], (real)bc.th[3]};
-    const real *pkb = pk + (size_t)T.b * Nz * 8;
-    z_load_rhs<real, KZ, MODE>(T, th, rho, Nr, Nz, rowcls, pkb, R, Z, bcv, lane);
-    real sb = real(0), sg = real(0);
+    const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    ZLane<real, V, MODE> L;
+    L.init(th, colcls, pkA, pkB, Nr, Nz, grp * 32 * V + lane * V, lane, bc);
+    real sb[V], sg[V];
 #pragma unroll
-    for (int k = 0; k < KZ; ++k) {
-        const int j = T.j0 + k;
-        if (T.col && j < T.j1) {
-            sb = fmad(T.d[k], pkb[(size_t)j * 8 + 3], sb);
-            sg = fmad(T.d[k], pkb[(size_t)j * 8 + 4], sg);
+    for (int q = 0; q < V; ++q) sb[q] = sg[q] = real(0);
+    z_walk<real, V, MODE>(L, rho, j0, j1, rowcls, R, [&](int, const real(&d)[V], const real(&)[V][4], const real(&eB)[V][4]) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            sb[q] = fmad(d[q], eB[q][2], sb[q]);
+            sg[q] = fmad(d[q], eB[q][3], sg[q]);
         }
-    }
-    sBs[w][lane] = sb;
-    sGs[w][lane] = sg;
-    __syncthreads();
-    if (w == 0 && T.col) {
-        real B = real(0), Gs = real(0);
-        for (int v = 0; v < NW; ++v) {
-            B += sBs[v][lane];
-            Gs += sGs[v][lane];
+    });
+    if (L.vec) {
+        if (L.any) {
+            VecIO<real, V>::st(zs + ((size_t)c * 2) * Nr + L.ib, sb);
+            VecIO<real, V>::st(zs + ((size_t)c * 2 + 1) * Nr + L.ib, sg);
         }
-        zsum[((size_t)c * 2) * Nr + T.i] = B;
-        zsum[((size_t)c * 2 + 1) * Nr + T.i] = Gs;
+    } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            if (L.ib + q < Nr) {
+                zs[((size_t)c * 2) * Nr + L.ib + q] = sb[q];
+                zs[((size_t)c * 2 + 1) * Nr + L.ib + q] = sg[q];
+            }
+        }
     }
 }
 
-// Pass 2: carries of this chunk from all chunk summaries of the column, then
-// the chunk solve (in-block carry scans over warps).
-template <typename real, int KZ, int MODE>
-__global__ void __launch_bounds__(512, 2) zsolve_kernel(const real *__restrict__ th, real *__restrict__ out,
-                                                     real *__restrict__ rho_out, const real *__restrict__ rho_in,
-                                                     int Nr, int Nz, int Rc, int nch, const int *__restrict__ rowcls,
-                                                     const int *__restrict__ colcls, const real *__restrict__ pk,
-                                                     const real *__restrict__ chk, LineTab<real> R, LineTab<real> Z,
-                                                     LineTab64 R64, LineTab64 Z64, BcVals bc,
-                                                     const real *__restrict__ zsum)
+// Pass 2: chunk carries of every column, one warp per column; lane l owns
+// chunks [l*M, (l+1)*M) (M <= ZM) and loads all it needs up front; the
+// carry recurrences across lanes are exclusive scans of affine maps.  Writes
+// cin_c = D_{c-1} and xin_c = X_{c+1} to zc[(c*2 + 0|1)*Nr + i].
+constexpr int ZM = 8;
+
+template <typename real>
+__global__ void __launch_bounds__(256) zcarry_kernel(int Nr, int nch, const int *__restrict__ colcls,
+                                                     const real *__restrict__ chk, const real *__restrict__ zs,
+                                                     real *__restrict__ zc)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *Dsm = reinterpret_cast<real *>(smem_raw);  // [nch][32]: D_{c'-1} per column
-    __shared__ real sF[16][33], sB[16][33], sEF[16][33], sEB[16][33];
-    __shared__ real cinS[32], xinS[32];
-    __shared__ double dLo[16][33], dHi[16][33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    const int c = blockIdx.y;
-    ZThread<real, KZ> T;
-    T.i = blockIdx.x * 32 + lane;
-    T.col = T.i < Nr;
-    T.b = T.col ? colcls[T.i] : 0;
-    const int r0 = c * Rc, r1 = min(Nz, r0 + Rc);
-    T.j0 = min(r0 + w * KZ, r1);
-    T.j1 = min(T.j0 + KZ, r1);
-    const real bcv[4] = {(real)bc.th[0], (real)bc.th[1], (real)bc.th[2], (real)bc.th[3]};
-    const real *pkb = pk + (size_t)T.b * Nz * 8;
-    const real *chb = chk + (size_t)T.b * nch * 4;
-
-    // carries into / out of this chunk, per column (warp 0)
-    if (w == 0) {
-        real D = real(0), X = real(0);
-        if (T.col) {
-            for (int cc = 0; cc < nch; ++cc) {
-                Dsm[cc * 32 + lane] = D;
-                if (cc < nch - 1) D = fmad(chb[cc * 4 + 0], D, zsum[((size_t)cc * 2) * Nr + T.i]);
-            }
-            for (int cc = nch - 1; cc > c; --cc)
-                X = fmad(chb[cc * 4 + 1], X,
-                         fmad(chb[cc * 4 + 2], Dsm[cc * 32 + lane], zsum[((size_t)cc * 2 + 1) * Nr + T.i]));
-        }
-        cinS[lane] = T.col ? Dsm[c * 32 + lane] : real(0);
-        xinS[lane] = X;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= Nr) return;  // warp-uniform
+    const real *chb = chk + (size_t)colcls[i] * nch * 4;
+    const int M = (nch + 31) / 32;
+    const int c0 = lane * M;
+    const size_t st = (size_t)2 * Nr;
+    real Bv[ZM], Gv[ZM], Fv[ZM], Hv[ZM], Pv[ZM];
+#pragma unroll
+    for (int u = 0; u < ZM; ++u) {
+        const int c = c0 + u;
+        const bool ok = u < M && c < nch;
+        Bv[u] = ok ? zs[c * st + i] : real(0);
+        Gv[u] = ok ? zs[c * st + Nr + i] : real(0);
+        Fv[u] = ok ? chb[c * 4 + 0] : real(1);
+        Hv[u] = ok ? chb[c * 4 + 1] : real(1);
+        Pv[u] = ok ? chb[c * 4 + 2] : real(0);
     }
-    z_load_rhs<real, KZ, MODE>(T, th, rho_in, Nr, Nz, rowcls, pkb, R, Z, bcv, lane);
-
-    // forward local
+    // forward: D_c = B_c + F_c D_{c-1}
     real F = real(1), B = real(0);
 #pragma unroll
-    for (int k = 0; k < KZ; ++k) {
-        const int j = T.j0 + k;
-        real iv = real(0), ff = real(0);
-        if (T.col && j < T.j1) {
-            iv = pkb[(size_t)j * 8 + 0];
-            ff = pkb[(size_t)j * 8 + 1];
-        }
-        B = fmad(T.d[k], iv, ff * B);
-        F *= ff;
+    for (int u = 0; u < ZM; ++u) {
+        B = fmad(Fv[u], B, Bv[u]);
+        F *= Fv[u];
     }
-    sF[w][lane] = F;
-    sB[w][lane] = B;
-    __syncthreads();
-    // exclusive scan over warps, one column per (warp, pass): lane p holds warp p's map
-    for (int cc = w; cc < 32; cc += NW) {
-        real f2 = lane < NW ? sF[lane][cc] : real(1), b2 = lane < NW ? sB[lane][cc] : real(0), fe, be;
-        seg_scan_fwd(f2, b2, fe, be, lane, 32);
-        if (lane < NW) {
-            sEF[lane][cc] = fe;
-            sEB[lane][cc] = be;
-        }
-    }
-    __syncthreads();
-    real dp = fmad(sEF[w][lane], cinS[lane], sEB[w][lane]);
+    real Fe, Be;
+    seg_scan_fwd(F, B, Fe, Be, lane, 32);
+    real Dv[ZM];  // D_{c-1} for each owned chunk
+    real D = Be;
 #pragma unroll
-    for (int k = 0; k < KZ; ++k) {
-        const int j = T.j0 + k;
-        real iv = real(0), ff = real(0);
-        if (T.col && j < T.j1) {
-            iv = pkb[(size_t)j * 8 + 0];
-            ff = pkb[(size_t)j * 8 + 1];
-        }
-        dp = fmad(T.d[k], iv, ff * dp);
-        T.d[k] = dp;
+    for (int u = 0; u < ZM; ++u) {
+        Dv[u] = D;
+        D = fmad(Fv[u], D, Bv[u]);
     }
+    // backward: X_c = (G0_c + GP_c D_{c-1}) + H_c X_{c+1}
     real H = real(1), Gm = real(0);
 #pragma unroll
-    for (int k = KZ - 1; k >= 0; --k) {
-        const int j = T.j0 + k;
-        const real cc = (T.col && j < T.j1) ? pkb[(size_t)j * 8 + 2] : real(0);
-        Gm = fmad(cc, Gm, T.d[k]);
-        H *= cc;
+    for (int u = ZM - 1; u >= 0; --u) {
+        Gm = fmad(Hv[u], Gm, fmad(Pv[u], Dv[u], Gv[u]));
+        H *= Hv[u];
     }
-    __syncthreads();
-    sF[w][lane] = H;
-    sB[w][lane] = Gm;
-    __syncthreads();
-    for (int cc = w; cc < 32; cc += NW) {
-        real h2 = lane < NW ? sF[lane][cc] : real(1), g2 = lane < NW ? sB[lane][cc] : real(0), he, ge;
-        seg_scan_bwd(h2, g2, he, ge, lane, 32);
-        if (lane < NW) {
-            sEF[lane][cc] = he;
-            sEB[lane][cc] = ge;
+    real He, Ge;
+    seg_scan_bwd(H, Gm, He, Ge, lane, 32);
+    real X = Ge;
+    real Xv[ZM];
+#pragma unroll
+    for (int u = ZM - 1; u >= 0; --u) {
+        Xv[u] = X;
+        X = fmad(Hv[u], X, fmad(Pv[u], Dv[u], Gv[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < ZM; ++u) {
+        const int c = c0 + u;
+        if (u < M && c < nch) {
+            zc[c * st + i] = Dv[u];
+            zc[c * st + Nr + i] = Xv[u];
         }
     }
-    __syncthreads();
-    real x = fmad(sEF[w][lane], xinS[lane], sEB[w][lane]);
+}
+
+// Pass 3: solve every (column, chunk) from its carries.  Shared memory holds
+// the forward results of each warp: [warps][Rc][32*V] reals.
+template <typename real, int V, int MODE>
+__global__ void __launch_bounds__(64) zsolve_kernel(const real *__restrict__ th, real *__restrict__ out,
+                                                    real *__restrict__ rho_out, const real *__restrict__ rho_in,
+                                                    int Nr, int Nz, int Rc, const int *__restrict__ rowcls,
+                                                    const int *__restrict__ colcls, const real *__restrict__ pkA,
+                                                    const real *__restrict__ pkB, LineTab<real> R, LineTab64 R64,
+                                                    LineTab64 Z64, BcVals bc, const real *__restrict__ zc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int COLS = 32 * V;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = blockIdx.x * (blockDim.x >> 5) + w;
+    if (grp * COLS >= Nr) return;  // whole warp past the field (warp-uniform)
+    const int c = blockIdx.y;
+    const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    real *dsm = reinterpret_cast<real *>(smem_raw) + (size_t)w * Rc * COLS + lane * V;
+    ZLane<real, V, MODE> L;
+    L.init(th, colcls, pkA, pkB, Nr, Nz, grp * COLS + lane * V, lane, bc);
+    real dp[V], x[V], cin[V];
 #pragma unroll
-    for (int k = KZ - 1; k >= 0; --k) {
-        const int j = T.j0 + k;
-        const real cc = (T.col && j < T.j1) ? pkb[(size_t)j * 8 + 2] : real(0);
-        x = fmad(cc, x, T.d[k]);
-        T.d[k] = x;
+    for (int q = 0; q < V; ++q) {
+        const bool in = L.ib + q < Nr;
+        cin[q] = in ? zc[((size_t)c * 2) * Nr + L.ib + q] : real(0);
+        x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + L.ib + q] : real(0);
+        dp[q] = cin[q];
+    }
+    z_walk<real, V, MODE>(L, rho_in, j0, j1, rowcls, R, [&](int j, const real(&d)[V], const real(&eA)[V][4], const real(&)[V][4]) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], eA[q][0], eA[q][1] * dp[q]);
+        VecIO<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
+    });
+    // backward from the carry-out, writing the solution rows
+    for (int j = j1 - 1; j >= j0; --j) {
+        real dd[V];
+        {
+            const real *p = dsm + (size_t)(j - j0) * COLS;
+#pragma unroll
+            for (int q = 0; q < V; ++q) dd[q] = p[q];
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const real cpq = (L.uni ? L.pa[0] : L.pa[q])[4 * j + 2];
+            x[q] = fmad(cpq, x[q], dd[q]);
+        }
+        if constexpr (MODE == MODE_REFINE) VecIO<real, V>::st(dsm + (size_t)(j - j0) * COLS, x);
+        if (!L.any) continue;
+        real o[V];
+        if constexpr (MODE == MODE_LIT) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) o[q] = x[q];
+        } else {
+            real base[V];
+            L.row(MODE == MODE_CORR ? out : th, j, base);
+#pragma unroll
+            for (int q = 0; q < V; ++q) o[q] = base[q] + x[q];
+        }
+        real *orow = out + (size_t)j * Nr + L.ib;
+        if (L.vec) {
+            VecIO<real, V>::st(orow, o);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+                if (L.ib + q < Nr) orow[q] = o[q];
+        }
     }
 
     if constexpr (MODE == MODE_REFINE) {
-        // FP64 residual of the increment system at the FP32 solution; the
-        // neighbours of the chunk ends come from the adjacent warps, or from
-        // the carries at the block's chunk ends:
-        //   x_{r0-1} = D_{c-1} + cp_{r0-1} x_{r0},   x_{r1} = X_{c+1}.
-        dLo[w][lane] = (double)T.d[0];
-        dHi[w][lane] = (double)T.d[KZ - 1];
-        __syncthreads();
-        double xm_end = 0.0, xp_end = 0.0;
-        const int i = T.i;
-        if (T.col) {
-            if (w > 0) {
-                xm_end = dHi[w - 1][lane];
-            } else if (r0 > 0) {
-                xm_end = (double)cinS[lane] + (double)pkb[(size_t)(r0 - 1) * 8 + 2] * (double)T.d[0];
-            }
-            if (T.j1 < r1) {
-                xp_end = dLo[w + 1][lane];
-            } else if (r1 < Nz) {
-                xp_end = (double)xinS[lane];
-            }
+        // FP64 residual of the increment system at the FP32 solution x (now in
+        // shared memory); outside the chunk: x_{j0-1} = D_{c-1} + cp_{j0-1} x_{j0}
+        // and x_{j1} = X_{c+1}.
+        const int ib = L.ib;
+        double xlo[V], xhi[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const bool in = ib + q < Nr;
+            const real x0 = dsm[q];
+            xlo[q] = (j0 > 0 && in) ? (double)cin[q] + (double)(L.uni ? L.pa[0] : L.pa[q])[4 * (j0 - 1) + 2] * (double)x0
+                                    : 0.0;
+            xhi[q] = (j1 < Nz && in) ? (double)zc[((size_t)c * 2 + 1) * Nr + ib + q] : 0.0;
+        }
+        double tm[V], t[V], tp[V];
+        {
+            real a0[V], a1[V];
+            L.row(th, j0 - 1, a0);
+            L.row(th, j0, a1);
+#pragma unroll
+            for (int q = 0; q < V; ++q) tm[q] = (double)a0[q], t[q] = (double)a1[q];
         }
         int a64 = -1;
-        double A0 = 0, A1 = 0, A2 = 0, A3 = 0;
-        double tprev = (T.col && T.j0 - 1 >= 0 && T.j0 - 1 < Nz) ? (double)th[(size_t)(T.j0 - 1) * Nr + i] : 0.0;
+        double A0[V], A1[V];
 #pragma unroll
-        for (int k = 0; k < KZ; ++k) {
-            const int j = T.j0 + k;
-            const bool vr = j < T.j1;
-            const double tcur = (double)T.t[k];
-            const double tnext = (T.col && j + 1 < Nz) ? (double)th[(size_t)(j + 1) * Nr + i] : 0.0;
-            const int a = vr ? rowcls[j] : a64;
-            if (a != a64 && vr) {
-                if (T.col) {
-                    const size_t ro = (size_t)a * Nr + i;
-                    A0 = R64.am[ro];
-                    A1 = R64.ap[ro];
-                    A2 = R64.dl[ro];
-                    A3 = R64.dh[ro];
-                }
+        for (int q = 0; q < V; ++q) A0[q] = A1[q] = 0.0;
+        for (int j = j0; j < j1; ++j) {
+            {
+                real a2[V];
+                L.row(th, j + 1, a2);
+#pragma unroll
+                for (int q = 0; q < V; ++q) tp[q] = (double)a2[q];
+            }
+            real tlr, trr;
+            {
+                real tt[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) tt[q] = (real)t[q];
+                L.halo(j, tt, tlr, trr);
+            }
+            const double tl = (double)tlr, tr = (double)trr;
+            const int a = rowcls[j];
+            if (a != a64) {
                 a64 = a;
-            }
-            double tl = __shfl_up_sync(HEAT_FULL_MASK, tcur, 1);
-            double tr = __shfl_down_sync(HEAT_FULL_MASK, tcur, 1);
-            if (lane == 0) tl = (T.col && i > 0 && vr) ? (double)th[(size_t)j * Nr + i - 1] : tcur;
-            if (lane == 31) tr = (i + 1 < Nr && vr) ? (double)th[(size_t)j * Nr + i + 1] : tcur;
-            if (T.col && vr) {
-                const size_t zj = (size_t)T.b * Nz + j;
-                double r = Z64.q[zj];
-                r = fma(Z64.am[zj], tprev - tcur, r);
-                r = fma(Z64.ap[zj], tnext - tcur, r);
-                r = fma(Z64.dl[zj], bc.th[2] - tcur, r);
-                r = fma(Z64.dh[zj], bc.th[3] - tcur, r);
-                r = fma(A0, tl - tcur, r);
-                r = fma(A1, tr - tcur, r);
-                r = fma(A2, bc.th[0] - tcur, r);
-                r = fma(A3, bc.th[1] - tcur, r);
-                const double xm = k > 0 ? (double)T.d[k - 1] : xm_end;
-                const double xp = k < KZ - 1 ? (double)T.d[k + 1] : xp_end;
-                const double rr = r - (Z64.b[zj] * (double)T.d[k] - Z64.m[zj] * xm - Z64.p[zj] * xp);
-                rho_out[(size_t)j * Nr + i] = (real)rr;
-            }
-            tprev = tcur;
-        }
-    }
-    if (T.col) {
 #pragma unroll
-        for (int k = 0; k < KZ; ++k) {
-            const int j = T.j0 + k;
-            if (j < T.j1) {
-                const size_t c2 = (size_t)j * Nr + T.i;
-                if constexpr (MODE == MODE_LIT)
-                    out[c2] = T.d[k];
-                else if constexpr (MODE == MODE_CORR)
-                    out[c2] = out[c2] + T.d[k];
-                else
-                    out[c2] = T.t[k] + T.d[k];
+                for (int q = 0; q < V; ++q) {
+                    const int i = ib + q;
+                    const size_t ro = (size_t)a * Nr + i;
+                    A0[q] = i < Nr ? (i == 0 ? R64.dl[ro] : R64.am[ro]) : 0.0;
+                    A1[q] = i < Nr ? (i == Nr - 1 ? R64.dh[ro] : R64.ap[ro]) : 0.0;
+                }
             }
+            real rr[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const size_t zj = (size_t)L.b[q] * Nz + j;
+                const double l = q > 0 ? t[q - 1] : tl;
+                const double r = q < V - 1 ? t[q + 1] : tr;
+                const double zm = j == 0 ? Z64.dl[zj] : Z64.am[zj];
+                const double zp = j == Nz - 1 ? Z64.dh[zj] : Z64.ap[zj];
+                double v = Z64.q[zj];
+                v = fma(zm, tm[q] - t[q], v);
+                v = fma(zp, tp[q] - t[q], v);
+                v = fma(A0[q], l - t[q], v);
+                v = fma(A1[q], r - t[q], v);
+                const real *xs = dsm + (size_t)(j - j0) * COLS;
+                const double xm = j > j0 ? (double)xs[q - COLS] : xlo[q];
+                const double xp = j + 1 < j1 ? (double)xs[q + COLS] : xhi[q];
+                rr[q] = (real)(v - (Z64.b[zj] * (double)xs[q] - Z64.m[zj] * xm - Z64.p[zj] * xp));
+            }
+            if (L.any) {
+                real *row = rho_out + (size_t)j * Nr + ib;
+                if (L.vec) {
+                    VecIO<real, V>::st(row, rr);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q)
+                        if (ib + q < Nr) row[q] = rr[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = tp[q];
         }
     }
 }
@@ -1006,28 +1158,38 @@ static cudaError_t launch_rsweep(const heat_ctx *ctx, const real *in, real *out,
     return rsweep_k<real, 32, MODE>(ctx, in, out, R, Z);
 }
 
-template <typename real, int KZ, int MODE>
+template <typename real, int MODE>
 static cudaError_t zsweep_pass(const heat_ctx *ctx, const real *in, real *out, real *rho_out, const real *rho_in,
-                               const LineTab<real> &R, const LineTab<real> &Z)
+                               const LineTab<real> &R, const LineTab<real> &)
 {
+    constexpr int V = 16 / (int)sizeof(real);
+    constexpr int COLS = 32 * V;
     const int Nr = ctx->g.Nr, Nz = ctx->g.Nz;
     const int Rc = ctx->zp.Rc, nch = ctx->zp.n_chunks;
-    const int NW = Rc / KZ;
-    const dim3 grid((Nr + 31) / 32, nch, 1);
-    const dim3 block(32 * NW, 1, 1);
+    const int groups = (Nr + COLS - 1) / COLS;
+    const real *pk = ZBufs<real>::pk(ctx);
+    const size_t npk = (size_t)ctx->Z.n_class * Nz;
+    const real *pkA = pk, *pkB = pk + 4 * npk;
     real *zs = ZBufs<real>::sum(ctx);
-    zsum_kernel<real, KZ, MODE><<<grid, block, 0, ctx->stream>>>(in, rho_in, Nr, Nz, Rc, ctx->d_rowcls,
-                                                                 ctx->d_colcls, ZBufs<real>::pk(ctx), R, Z,
-                                                                 bc_vals(ctx), zs);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)nch * 32 * sizeof(real);
-    auto kern = zsolve_kernel<real, KZ, MODE>;
+    real *zc = zs + (size_t)2 * nch * Nr;
+    cudaError_t e;
+    {
+        constexpr int WPB = 4;
+        const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
+        zsum_kernel<real, V, MODE><<<grid, 32 * WPB, 0, ctx->stream>>>(in, rho_in, Nr, Nz, Rc, ctx->d_rowcls,
+                                                                      ctx->d_colcls, pkA, pkB, R, bc_vals(ctx), zs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    zcarry_kernel<real><<<(Nr + 7) / 8, 256, 0, ctx->stream>>>(Nr, nch, ctx->d_colcls, ZBufs<real>::ch(ctx), zs, zc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int WPB = (size_t)Rc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
+    const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
+    auto kern = zsolve_kernel<real, V, MODE>;
+    const size_t smem = (size_t)WPB * Rc * COLS * sizeof(real);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    kern<<<grid, block, smem, ctx->stream>>>(in, out, rho_out, rho_in, Nr, Nz, Rc, nch, ctx->d_rowcls, ctx->d_colcls,
-                                             ZBufs<real>::pk(ctx), ZBufs<real>::ch(ctx), R, Z, ctx->dR.full,
-                                             ctx->dZ.full, bc_vals(ctx), zs);
+    kern<<<grid, 32 * WPB, smem, ctx->stream>>>(in, out, rho_out, rho_in, Nr, Nz, Rc, ctx->d_rowcls, ctx->d_colcls, pkA,
+                                                pkB, R, ctx->dR.full, ctx->dZ.full, bc_vals(ctx), zc);
     return cudaGetLastError();
 }
 
@@ -1035,16 +1197,15 @@ template <typename real, int MODE>
 static cudaError_t launch_zsweep(const heat_ctx *ctx, const real *in, real *out, const LineTab<real> &R,
                                  const LineTab<real> &Z)
 {
-    if constexpr (sizeof(real) == 8) {
-        return zsweep_pass<real, 8, MODE>(ctx, in, out, nullptr, nullptr, R, Z);
-    } else if constexpr (MODE == MODE_REFINE) {
-        cudaError_t e = zsweep_pass<real, 16, MODE_REFINE>(ctx, in, out, ctx->d_rho, nullptr, R, Z);
+    if constexpr (MODE == MODE_REFINE) {
+        cudaError_t e = zsweep_pass<real, MODE_REFINE>(ctx, in, out, ctx->d_rho, nullptr, R, Z);
         if (e != cudaSuccess) return e;
-        return zsweep_pass<real, 16, MODE_CORR>(ctx, in, out, nullptr, ctx->d_rho, R, Z);
+        return zsweep_pass<real, MODE_CORR>(ctx, in, out, nullptr, ctx->d_rho, R, Z);
     } else {
-        return zsweep_pass<real, 16, MODE>(ctx, in, out, nullptr, nullptr, R, Z);
+        return zsweep_pass<real, MODE>(ctx, in, out, nullptr, nullptr, R, Z);
     }
 }
+
 template <typename real, int MODE>
 static cudaError_t sweep_mode(heat_ctx *ctx, int dir, const real *a, real *b, const LineTab<real> &R,
                               const LineTab<real> &Z)

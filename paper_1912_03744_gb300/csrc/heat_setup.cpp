@@ -25,7 +25,7 @@ void HostTab::resize(int nc, int n)
     n_class = nc;
     N = n;
     size_t sz = (size_t)nc * n;
-    for (auto *v : {&inv, &f, &cp, &w, &s, &am, &ap, &ad, &sd, &dl, &dh, &q, &m, &b, &p, &cap, &dsum, &dbc, &ssum})
+    for (auto *v : {&inv, &f, &cp, &w, &s, &am, &ap, &ad, &sd, &dl, &dh, &q, &xm, &xp, &m, &b, &p, &cap, &dsum, &dbc, &ssum})
         v->assign(sz, 0.0);
 }
 
@@ -48,9 +48,9 @@ int validate(const heat_geometry *g, const heat_materials *mt, const heat_option
         if (!(g->z_faces[l + 1] > g->z_faces[l]) || g->z_cells[l] < 1) return HEAT_ERR_ARG;
         Nz += g->z_cells[l];
     }
-    // r-lines are solved by one block of <= 1024 threads x <= 32 cells; the
-    // z-sweep keeps one carry per column chunk in shared memory (<= 512 chunks)
-    if (Nr > 32768 || Nz > 65536 || Nr * Nz > (1LL << 34)) return HEAT_ERR_ARG;
+    // r-lines are solved by one block of <= 1024 threads x <= 32 cells; a
+    // z chunk of <= 128 rows x 128 columns fits one block's shared memory
+    if (Nr > 32768 || Nz > 32768 || Nr * Nz > (1LL << 34)) return HEAT_ERR_ARG;
     for (int f = 0; f < 4; ++f)
         if ((g->bc[f] != HEAT_BC_NEUMANN && g->bc[f] != HEAT_BC_DIRICHLET) || !std::isfinite(g->T_bc[f]))
             return HEAT_ERR_ARG;
@@ -195,6 +195,8 @@ static void fill_class(HostTab &T, int cls, const std::vector<int> &reg, const s
         T.sd[o + x] = Dl * th_lo + Dh * th_hi;
         T.dl[o + x] = Dl;
         T.dh[o + x] = Dh;
+        T.xm[o + x] = x == 0 ? Dl : m;
+        T.xp[o + x] = x == N - 1 ? Dh : p;
         T.q[o + x] = act ? ctx->q[r] : 0.0;
         T.cap[o + x] = act ? ctx->C[r] : 0.0;
         T.dsum[o + x] = Dl + Dh;
@@ -235,8 +237,40 @@ void build_tables(heat_ctx *ctx)
     }
 }
 
-// Packed z-sweep tables and chunk constants for the column partition (see
-// ZPart in heat_internal.h); FP64 on the host.
+// Packed z-sweep tables, chunk and run constants for the column partition
+// (see ZPart in heat_internal.h); FP64 on the host.
+static void segment_weights(const HostTab &Z, size_t o, int r0, int r1, double *wB, double *wG, double *Cout,
+                            double *F, double *H, double *GP)
+{
+    const int n = r1 - r0;
+    std::vector<double> C(n + 1), P(n), S(n + 1);
+    C[0] = 1.0;
+    for (int k = 0; k < n; ++k) C[k + 1] = C[k] * Z.cp[o + r0 + k];
+    double pp = 1.0;
+    for (int k = 0; k < n; ++k) {
+        pp *= Z.f[o + r0 + k];
+        P[k] = pp;
+    }
+    double tail = 1.0;
+    for (int k = n - 1; k >= 0; --k) {
+        wB[k] = Z.inv[o + r0 + k] * tail;
+        tail *= Z.f[o + r0 + k];
+    }
+    S[n] = 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+        const double fn = k + 1 < n ? Z.f[o + r0 + k + 1] : 0.0;
+        S[k] = C[k] + fn * S[k + 1];
+        if (wG) wG[k] = Z.inv[o + r0 + k] * S[k];
+    }
+    double gp = 0.0;
+    for (int k = 0; k < n; ++k) gp += P[k] * C[k];
+    if (Cout)
+        for (int k = 0; k < n; ++k) Cout[k] = C[k];
+    *F = P[n - 1];
+    *H = C[n];
+    if (GP) *GP = gp;
+}
+
 void build_zpartition(heat_ctx *ctx)
 {
     const HostTab &Z = ctx->Z;
@@ -248,49 +282,27 @@ void build_zpartition(heat_ctx *ctx)
     ctx->zpk.assign((size_t)nb * Nz * 8, 0.0);
     ctx->zch.assign((size_t)nb * nch * 4, 0.0);
     const bool lit = ctx->precision == HEAT_FP64;
-    std::vector<double> C(Rc + 1), P(Rc), S(Rc + 1);
+    std::vector<double> wB(Rc), wG(Rc);
     for (int b = 0; b < nb; ++b) {
         const size_t o = (size_t)b * Nz;
         for (int c = 0; c < nch; ++c) {
-            const int r0 = c * Rc, r1 = std::min(Nz, r0 + Rc), n = r1 - r0;
-            // C_k = prod_{m=r0}^{k-1} cp_m, P_k = prod_{m=r0}^{k} f_m (local index k - r0)
-            C[0] = 1.0;
-            for (int k = 0; k < n; ++k) C[k + 1] = C[k] * Z.cp[o + r0 + k];
-            double pp = 1.0;
-            for (int k = 0; k < n; ++k) {
-                pp *= Z.f[o + r0 + k];
-                P[k] = pp;
-            }
-            // wB_j = inv_j prod_{m=j+1}^{r1-1} f_m
-            double tail = 1.0;
-            for (int k = n - 1; k >= 0; --k) {
-                double *e = &ctx->zpk[(o + r0 + k) * 8];
-                e[3] = Z.inv[o + r0 + k] * tail;
-                tail *= Z.f[o + r0 + k];
-            }
-            // S_j = C_j + f_{j+1} S_{j+1}, wG_j = inv_j S_j
-            S[n] = 0.0;
-            for (int k = n - 1; k >= 0; --k) {
-                const double fn = k + 1 < n ? Z.f[o + r0 + k + 1] : 0.0;
-                S[k] = C[k] + fn * S[k + 1];
-                ctx->zpk[(o + r0 + k) * 8 + 4] = Z.inv[o + r0 + k] * S[k];
-            }
-            double gp = 0.0;
-            for (int k = 0; k < n; ++k) gp += P[k] * C[k];
+            const int r0 = c * Rc, r1 = std::min(Nz, r0 + Rc);
             double *ch = &ctx->zch[((size_t)b * nch + c) * 4];
-            ch[0] = P[n - 1];
-            ch[1] = C[n];
-            ch[2] = gp;
-            ch[3] = 0.0;
+            segment_weights(Z, o, r0, r1, wB.data(), wG.data(), nullptr, &ch[0], &ch[1], &ch[2]);
+            for (int k = 0; k < r1 - r0; ++k) {
+                double *e = &ctx->zpk[(o + r0 + k) * 8];
+                e[6] = wB[k];
+                e[7] = wG[k];
+            }
         }
         for (int j = 0; j < Nz; ++j) {
             double *e = &ctx->zpk[(o + j) * 8];
             e[0] = Z.inv[o + j];
             e[1] = Z.f[o + j];
             e[2] = Z.cp[o + j];
-            e[5] = lit ? Z.w[o + j] : Z.am[o + j];
-            e[6] = lit ? Z.s[o + j] : Z.ap[o + j];
-            e[7] = lit ? 0.0 : Z.q[o + j];
+            e[3] = lit ? Z.s[o + j] : Z.q[o + j];
+            e[4] = lit ? Z.w[o + j] : Z.xm[o + j];
+            e[5] = lit ? 0.0 : Z.xp[o + j];
         }
     }
 }

@@ -31,8 +31,8 @@ cudaError_t launch_steps(heat_ctx *ctx, int n)
     return cudaSuccess;
 }
 
-// r-sweep: 1 launch; z-sweep: 2 (summaries, solve), 4 on the refined path.
-int launches_per_step(const heat_ctx *ctx) { return ctx->precision == HEAT_FP32_REFINED ? 5 : 3; }
+// r-sweep: 1 launch; z-sweep: 3 (summaries, carries, solve), 6 on the refined path.
+int launches_per_step(const heat_ctx *ctx) { return ctx->precision == HEAT_FP32_REFINED ? 7 : 4; }
 
 int energy_blocks(const heat_ctx *ctx)
 {

@@ -206,20 +206,30 @@ def test_full_size_config2_few_steps(precision):
     assert _rel(Tg, To) <= TOL[precision]
 
 
-def test_refined_path_is_more_accurate_at_high_contrast():
-    """Config 4's 1e4 conductivity contrast on a 512 x 1024 grid, 50 steps:
-    the FP64-residual refined FP32 path is at least as close to the oracle
-    as the plain FP32 path, and both meet the FP32 bar."""
+def test_refined_path_reduces_the_solve_error_at_high_contrast():
+    """Config 4's 1e4 conductivity contrast on a 512 x 1024 grid: one half-step
+    from T = T_init (increment = the implicit solve of the source term).  The
+    plain FP32 factorization leaves an error ~ kappa * eps in the increment;
+    one FP64-residual correction brings it to ~ eps (storage rounding).
+    After 50 full steps both FP32 paths stay within the FP32 bar."""
     p = H.config4(512, 1024)
     o = Oracle(p)
     tau = H.DT_FACTOR * o.tau_exp()
-    o.step(tau, 50)
-    To = o.field()
+    o.step(tau)
+    inc_o = o.half_field() - p.T_init
     errs = {}
     for prec in ("fp32", "fp32_refined"):
         s = _solver(p, tau, prec)
-        s.step(50)
-        errs[prec] = _rel(s.field(), To)
+        s.sweep(0)
+        errs[prec] = _rel(s.field() - p.T_init, inc_o)
+        s.sweep(1)
+        s.step(49)
         s.close()
-    assert errs["fp32_refined"] <= errs["fp32"] * 1.01, errs
-    assert max(errs.values()) <= 1e-5, errs
+    assert errs["fp32_refined"] <= 0.5 * errs["fp32"], errs
+    o2 = Oracle(p)
+    o2.step(tau, 50)
+    for prec in ("fp32", "fp32_refined"):
+        s = _solver(p, tau, prec)
+        s.step(50)
+        assert _rel(s.field(), o2.field()) <= 1e-5
+        s.close()
