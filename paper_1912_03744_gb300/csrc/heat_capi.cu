@@ -1,6 +1,7 @@
 // heat_capi.cu -- the extern "C" entry points of libheat.so (declared and
 // documented in include/heat.h).  Host-side orchestration only: every cell
 // of every step is computed by the kernels in heat_sweeps.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -104,6 +105,19 @@ int upload_zpart_t(heat_ctx *ctx, real *&pk, real *&ch)
 int upload_zpart(heat_ctx *ctx)
 {
     ZPart &z = ctx->zp;
+    {
+        std::vector<int> u(z.n_chunks);
+        for (int c = 0; c < z.n_chunks; ++c) {
+            const int r0 = c * z.Rc, r1 = std::min(ctx->g.Nz, r0 + z.Rc);
+            int a = ctx->g.rowcls[r0];
+            for (int j = r0; j < r1; ++j)
+                if (ctx->g.rowcls[j] != a) a = -1;
+            u[c] = a;
+        }
+        if (z.ucls) cudaFree(z.ucls), z.ucls = nullptr;
+        HEAT_CHECK(cudaMalloc(&z.ucls, u.size() * sizeof(int)));
+        HEAT_CHECK(cudaMemcpyAsync(z.ucls, u.data(), u.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
     const size_t nsum = (size_t)z.n_chunks * 4 * ctx->g.Nr;  // summaries [nch][2][Nr] + carries [nch][2][Nr]
     if (ctx->precision == HEAT_FP64) {
         int st = upload_zpart_t<double>(ctx, z.pk64, z.ch64);
@@ -123,7 +137,7 @@ void free_ctx(heat_ctx *ctx)
     void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32,   ctx->dZ.buf64,   ctx->dZ.buf32, ctx->d_rowcls,
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
-                    ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho};
+                    ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;

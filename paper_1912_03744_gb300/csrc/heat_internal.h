@@ -93,6 +93,7 @@ struct ZPart {
     int Rc = 0, n_chunks = 0;
     double *pk64 = nullptr, *ch64 = nullptr;  // device
     float *pk32 = nullptr, *ch32 = nullptr;   // device (FP32 paths)
+    int *ucls = nullptr;                      // device: row class of chunk c if all its rows share it, else -1
 };
 
 // Rows per z chunk (one warp walks a chunk of its columns): 32, or more

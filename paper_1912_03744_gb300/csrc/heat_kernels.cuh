@@ -549,15 +549,20 @@ struct ZLane {
     bool any, vec, uni, lo_edge, hi_edge;
     int b[V];
     const real *pa[V], *pb[V];  // packed table rows of each column's class at row 0
+    const real *stg;             // this warp's staged rows [Rc][8] of class bw (shared memory)
+    int bw, jst;                 // staged class and first staged row
+    bool allstg;                 // every column of the lane has class bw
     int acur;
     real ra[V], rb[V], rc[V], rd[V];  // increment: xm, xp; literal: am, ap, ad, sd
     real bz_lo, bz_hi, br_lo, br_hi;   // ghost values beyond the outer faces
 
+    const real *pkA_base, *pkB_base;
     __device__ __forceinline__ void init(const real *th_, const int *__restrict__ colcls, const real *__restrict__ pkA,
                                          const real *__restrict__ pkB, int Nr_, int Nz_, int ib_, int lane_,
                                          const BcVals &bc)
     {
         th = th_, Nr = Nr_, Nz = Nz_, ib = ib_, lane = lane_;
+        pkA_base = pkA, pkB_base = pkB;
         any = ib < Nr;
         vec = (Nr % V) == 0;
         lo_edge = ib == 0;
@@ -632,25 +637,51 @@ struct ZLane {
         if (lo_edge) tl = br_lo;
         if (hi_edge) tr = br_hi;
     }
-    // packed table entries of row j for column q
-    __device__ __forceinline__ void tables(int j, real (&eA)[V][4], real (&eB)[V][4]) const
+    // Stage the warp's table rows [j0, j1) of class bw (lane 0's first column)
+    // into shared memory: 8 reals per row (pkA then pkB).
+    __device__ __forceinline__ void stage(real *buf, int j0, int j1)
     {
-        ld4<real>(pa[0] + 4 * j, eA[0]);
-        ld4<real>(pb[0] + 4 * j, eB[0]);
+        bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
+        jst = j0;
+        stg = buf;
+        allstg = true;
 #pragma unroll
-        for (int q = 1; q < V; ++q) {
-            if (uni) {
+        for (int q = 0; q < V; ++q) allstg = allstg && b[q] == bw;
+        const real *A = pkA_base + (size_t)bw * Nz * 4, *B = pkB_base + (size_t)bw * Nz * 4;
+        for (int e = lane; e < (j1 - j0) * 8; e += 32) {
+            const int r = e >> 3, u = e & 7;
+            buf[e] = u < 4 ? A[4 * (j0 + r) + u] : B[4 * (j0 + r) + u - 4];
+        }
+        __syncwarp();
+    }
+    // the staged 8 table values of row j (lanes with allstg)
+    __device__ __forceinline__ void srow(int j, real (&e)[8]) const
+    {
+        const real *p = stg + (j - jst) * 8;
+        if constexpr (sizeof(real) == 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(p), c = *reinterpret_cast<const float4 *>(p + 4);
+            e[0] = a.x, e[1] = a.y, e[2] = a.z, e[3] = a.w, e[4] = c.x, e[5] = c.y, e[6] = c.z, e[7] = c.w;
+        } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) eA[q][u] = eA[0][u], eB[q][u] = eB[0][u];
-            } else {
-                ld4<real>(pa[q] + 4 * j, eA[q]);
-                ld4<real>(pb[q] + 4 * j, eB[q]);
+            for (int u = 0; u < 8; u += 2) {
+                const double2 a = *reinterpret_cast<const double2 *>(p + u);
+                e[u] = a.x, e[u + 1] = a.y;
             }
         }
     }
-    // right-hand side of row j from rows j-1, j, j+1 and the row neighbours
-    __device__ __forceinline__ void rhs(const real (&tm)[V], const real (&t)[V], const real (&tp)[V], real tl, real tr,
-                                        const real (&eA)[V][4], const real (&eB)[V][4], real (&d)[V]) const
+    // entry u of table A / B of row j for column q
+    __device__ __forceinline__ real tA(int q, int j, int u) const
+    {
+        return b[q] == bw ? stg[(j - jst) * 8 + u] : pa[q][4 * j + u];
+    }
+    __device__ __forceinline__ real tB(int q, int j, int u) const
+    {
+        return b[q] == bw ? stg[(j - jst) * 8 + 4 + u] : pb[q][4 * j + u];
+    }
+    // right-hand side of row j from rows j-1, j, j+1 and the row neighbours;
+    // e[q][0..7] are the table values of column q (pkA then pkB)
+    __device__ __forceinline__ void rhs(const real (&tm)[V], const real (&t)[V], const real (&tp)[V], real tl,
+                                        real tr, const real (&e)[V][8], real (&d)[V]) const
     {
 #pragma unroll
         for (int q = 0; q < V; ++q) {
@@ -658,15 +689,33 @@ struct ZLane {
             const real l = q > 0 ? t[q - 1] : tl;
             const real r = q < V - 1 ? t[q + 1] : tr;
             if constexpr (LIT) {
-                // eA[3] = s, eB[0] = w
-                d[q] = fmad(eB[q][0] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, eA[q][3] + rd[q])));
+                // A[3] = s, B[0] = w
+                d[q] = fmad(e[q][4] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, e[q][3] + rd[q])));
             } else {
-                // eA[3] = q, eB[0] = xm (z), eB[1] = xp (z)
-                real v = fmad(eB[q][0], tm[q] - x, eA[q][3]);
-                v = fmad(eB[q][1], tp[q] - x, v);
+                // A[3] = q, B[0] = xm (z), B[1] = xp (z)
+                real v = fmad(e[q][4], tm[q] - x, e[q][3]);
+                v = fmad(e[q][5], tp[q] - x, v);
                 v = fmad(ra[q], l - x, v);
                 d[q] = fmad(rb[q], r - x, v);
             }
+        }
+    }
+    // table values of row j for every column: one staged row when the lane's
+    // columns share the staged class, else per column
+    __device__ __forceinline__ void trow(int j, real (&e)[V][8]) const
+    {
+        if (allstg) {
+            real s8[8];
+            srow(j, s8);
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) e[q][u] = s8[u];
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) e[q][u] = tA(q, j, u), e[q][4 + u] = tB(q, j, u);
         }
     }
 };
@@ -677,53 +726,73 @@ struct ZLane {
 // lane has ZP rows of loads in flight.
 constexpr int ZP = 4;
 
+// Row pointer walk: rows are read through an incrementing pointer; the ghost
+// row beyond the top face is substituted once at the end of the column.
 template <typename real, int V, int MODE, typename Emit>
 __device__ __forceinline__ void z_walk(ZLane<real, V, MODE> &L, const real *__restrict__ rho, int j0, int j1,
-                                       const int *__restrict__ rowcls, const LineTab<real> &R, Emit emit)
+                                       int ucls, const int *__restrict__ rowcls, const LineTab<real> &R, Emit emit)
 {
+    const int Nr = L.Nr;
+    const bool fast = L.vec && L.any;
     real tm[V], t[V];
     if constexpr (MODE != MODE_CORR) {
         L.row(L.th, j0 - 1, tm);
         L.row(L.th, j0, t);
+        if (ucls >= 0) L.row_class(ucls, R);
     }
+    // halo pointers: the neighbours left / right of the warp's columns
+    const bool hasl = L.lane == 0 && L.ib > 0 && L.ib - 1 < Nr;
+    const bool hasr = L.lane == 31 && L.ib + V < Nr;
+    const real *src = MODE == MODE_CORR ? rho : L.th;
+    const int lead = MODE == MODE_CORR ? 0 : 1;  // rows ahead of j that the walk needs
+    const real *np = src + (size_t)(j0 + lead) * Nr + L.ib;
+    const real *hlp = L.th + (size_t)j0 * Nr + L.ib - 1;
+    const real *hrp = L.th + (size_t)j0 * Nr + L.ib + V;
     for (int jb = j0; jb < j1; jb += ZP) {
-        real nx[ZP][V], eA[ZP][V][4], eB[ZP][V][4], hl[ZP], hr[ZP];
-        int cls[ZP];
+        real nx[ZP][V], hl[ZP], hr[ZP];
 #pragma unroll
         for (int p = 0; p < ZP; ++p) {
-            const int j = jb + p;
-            const int jj = j < j1 ? j : j1 - 1;
-            L.tables(jj, eA[p], eB[p]);
-            if constexpr (MODE == MODE_CORR) {
-                L.row(rho, jj, nx[p]);
+            const int jn = jb + p + lead;  // row loaded into nx[p]
+            const bool ok = jn < L.Nz && jb + p < j1;
+            if (fast && ok) {
+                VecIO<real, V>::ld(np, nx[p]);
+            } else if (ok) {
+#pragma unroll
+                for (int q = 0; q < V; ++q) nx[p][q] = L.ib + q < Nr ? np[q] : L.br_hi;
             } else {
-                L.row(L.th, j + 1, nx[p]);
-                cls[p] = rowcls[jj];
-                hl[p] = (L.lane == 0 && L.ib > 0 && L.ib - 1 < L.Nr) ? L.th[(size_t)jj * L.Nr + L.ib - 1] : real(0);
-                hr[p] = (L.lane == 31 && L.ib + V < L.Nr) ? L.th[(size_t)jj * L.Nr + L.ib + V] : real(0);
+#pragma unroll
+                for (int q = 0; q < V; ++q) nx[p][q] = L.bz_hi;
+            }
+            np += Nr;
+            if constexpr (MODE != MODE_CORR) {
+                hl[p] = (hasl && jb + p < j1) ? *hlp : real(0);
+                hr[p] = (hasr && jb + p < j1) ? *hrp : real(0);
+                hlp += Nr;
+                hrp += Nr;
             }
         }
 #pragma unroll
         for (int p = 0; p < ZP; ++p) {
             const int j = jb + p;
             if (j >= j1) break;
-            real d[V];
+            real d[V], e[V][8];
+            L.trow(j, e);
             if constexpr (MODE == MODE_CORR) {
 #pragma unroll
                 for (int q = 0; q < V; ++q) d[q] = nx[p][q];
             } else {
                 real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
                 real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
-                if (L.lane == 0 && L.ib > 0) tl = hl[p];
-                if (L.lane == 31 && L.ib + V < L.Nr) tr = hr[p];
+                if (hasl) tl = hl[p];
+                if (hasr) tr = hr[p];
                 if (L.lo_edge) tl = L.br_lo;
                 if (L.hi_edge) tr = L.br_hi;
-                L.row_class(cls[p], R);
-                L.rhs(tm, t, nx[p], tl, tr, eA[p], eB[p], d);
+                if (ucls < 0) L.row_class(rowcls[j], R);
+                L.rhs(tm, t, nx[p], tl, tr, e, d);
 #pragma unroll
                 for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = nx[p][q];
             }
-            emit(j, d, eA[p], eB[p]);
+            emit(j, d, e);
         }
     }
 }
@@ -731,8 +800,9 @@ __device__ __forceinline__ void z_walk(ZLane<real, V, MODE> &L, const real *__re
 // Pass 1: summaries B = sum r wB and G0 = sum r wG of every (column, chunk):
 // zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks).
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(128) zsum_kernel(const real *__restrict__ th, const real *__restrict__ rho, int Nr,
-                                                   int Nz, int Rc, const int *__restrict__ rowcls,
+__global__ void __launch_bounds__(128, 4) zsum_kernel(const real *__restrict__ th, const real *__restrict__ rho, int Nr,
+                                                   int Nz, int Rc, const int *__restrict__ ucls,
+                                                   const int *__restrict__ rowcls,
                                                    const int *__restrict__ colcls, const real *__restrict__ pkA,
                                                    const real *__restrict__ pkB, LineTab<real> R, BcVals bc,
                                                    real *__restrict__ zs)
@@ -742,16 +812,18 @@ __global__ void __launch_bounds__(128) zsum_kernel(const real *__restrict__ th, 
     if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     ZLane<real, V, MODE> L;
     L.init(th, colcls, pkA, pkB, Nr, Nz, grp * 32 * V + lane * V, lane, bc);
+    L.stage(reinterpret_cast<real *>(smem_raw) + (size_t)(threadIdx.x >> 5) * Rc * 8, j0, j1);
     real sb[V], sg[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) sb[q] = sg[q] = real(0);
-    z_walk<real, V, MODE>(L, rho, j0, j1, rowcls, R, [&](int, const real(&d)[V], const real(&)[V][4], const real(&eB)[V][4]) {
+    z_walk<real, V, MODE>(L, rho, j0, j1, ucls[c], rowcls, R, [&](int, const real(&d)[V], const real(&e)[V][8]) {
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            sb[q] = fmad(d[q], eB[q][2], sb[q]);
-            sg[q] = fmad(d[q], eB[q][3], sg[q]);
+            sb[q] = fmad(d[q], e[q][6], sb[q]);
+            sg[q] = fmad(d[q], e[q][7], sg[q]);
         }
     });
     if (L.vec) {
@@ -770,83 +842,71 @@ __global__ void __launch_bounds__(128) zsum_kernel(const real *__restrict__ th, 
     }
 }
 
-// Pass 2: chunk carries of every column, one warp per column; lane l owns
-// chunks [l*M, (l+1)*M) (M <= ZM) and loads all it needs up front; the
-// carry recurrences across lanes are exclusive scans of affine maps.  Writes
-// cin_c = D_{c-1} and xin_c = X_{c+1} to zc[(c*2 + 0|1)*Nr + i].
-constexpr int ZM = 8;
+// Pass 2: chunk carries.  A block of ZSEG warps serves 32 columns (lane =
+// column: every access is coalesced); warp s runs the carry recurrences over
+// chunks [s*m, (s+1)*m) and the segments are joined through shared memory
+// (composition of the segments' affine maps).  Writes cin_c = D_{c-1} and
+// xin_c = X_{c+1} to zc[(c*2 + 0|1)*Nr + i].
+constexpr int ZSEG = 8;
 
 template <typename real>
-__global__ void __launch_bounds__(256) zcarry_kernel(int Nr, int nch, const int *__restrict__ colcls,
-                                                     const real *__restrict__ chk, const real *__restrict__ zs,
-                                                     real *__restrict__ zc)
+__global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(int Nr, int nch, const int *__restrict__ colcls,
+                                                           const real *__restrict__ chk, const real *__restrict__ zs,
+                                                           real *__restrict__ zc)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= Nr) return;  // warp-uniform
-    const real *chb = chk + (size_t)colcls[i] * nch * 4;
-    const int M = (nch + 31) / 32;
-    const int c0 = lane * M;
+    __shared__ real sF[ZSEG][32], sB[ZSEG][32];
+    const int lane = threadIdx.x & 31, sgm = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const bool col = i < Nr;
+    const real *chb = chk + (size_t)(col ? colcls[i] : 0) * nch * 4;
+    const int m = (nch + ZSEG - 1) / ZSEG;
+    const int c0 = min(sgm * m, nch), c1 = min(c0 + m, nch);
     const size_t st = (size_t)2 * Nr;
-    real Bv[ZM], Gv[ZM], Fv[ZM], Hv[ZM], Pv[ZM];
-#pragma unroll
-    for (int u = 0; u < ZM; ++u) {
-        const int c = c0 + u;
-        const bool ok = u < M && c < nch;
-        Bv[u] = ok ? zs[c * st + i] : real(0);
-        Gv[u] = ok ? zs[c * st + Nr + i] : real(0);
-        Fv[u] = ok ? chb[c * 4 + 0] : real(1);
-        Hv[u] = ok ? chb[c * 4 + 1] : real(1);
-        Pv[u] = ok ? chb[c * 4 + 2] : real(0);
-    }
-    // forward: D_c = B_c + F_c D_{c-1}
+    // forward segment map
     real F = real(1), B = real(0);
-#pragma unroll
-    for (int u = 0; u < ZM; ++u) {
-        B = fmad(Fv[u], B, Bv[u]);
-        F *= Fv[u];
-    }
-    real Fe, Be;
-    seg_scan_fwd(F, B, Fe, Be, lane, 32);
-    real Dv[ZM];  // D_{c-1} for each owned chunk
-    real D = Be;
-#pragma unroll
-    for (int u = 0; u < ZM; ++u) {
-        Dv[u] = D;
-        D = fmad(Fv[u], D, Bv[u]);
-    }
-    // backward: X_c = (G0_c + GP_c D_{c-1}) + H_c X_{c+1}
-    real H = real(1), Gm = real(0);
-#pragma unroll
-    for (int u = ZM - 1; u >= 0; --u) {
-        Gm = fmad(Hv[u], Gm, fmad(Pv[u], Dv[u], Gv[u]));
-        H *= Hv[u];
-    }
-    real He, Ge;
-    seg_scan_bwd(H, Gm, He, Ge, lane, 32);
-    real X = Ge;
-    real Xv[ZM];
-#pragma unroll
-    for (int u = ZM - 1; u >= 0; --u) {
-        Xv[u] = X;
-        X = fmad(Hv[u], X, fmad(Pv[u], Dv[u], Gv[u]));
-    }
-#pragma unroll
-    for (int u = 0; u < ZM; ++u) {
-        const int c = c0 + u;
-        if (u < M && c < nch) {
-            zc[c * st + i] = Dv[u];
-            zc[c * st + Nr + i] = Xv[u];
+    if (col)
+        for (int c = c0; c < c1; ++c) {
+            const real Fc = chb[c * 4];
+            B = fmad(Fc, B, zs[c * st + i]);
+            F *= Fc;
         }
-    }
+    sF[sgm][lane] = F;
+    sB[sgm][lane] = B;
+    __syncthreads();
+    real D = real(0);
+    for (int v = 0; v < sgm; ++v) D = fmad(sF[v][lane], D, sB[v][lane]);
+    if (col)
+        for (int c = c0; c < c1; ++c) {
+            zc[c * st + i] = D;
+            D = fmad(chb[c * 4], D, zs[c * st + i]);
+        }
+    // backward segment map X_c = (G0_c + GP_c D_{c-1}) + H_c X_{c+1}
+    real H = real(1), Gm = real(0);
+    if (col)
+        for (int c = c1 - 1; c >= c0; --c) {
+            Gm = fmad(chb[c * 4 + 1], Gm, fmad(chb[c * 4 + 2], zc[c * st + i], zs[c * st + Nr + i]));
+            H *= chb[c * 4 + 1];
+        }
+    __syncthreads();
+    sF[sgm][lane] = H;
+    sB[sgm][lane] = Gm;
+    __syncthreads();
+    real X = real(0);
+    for (int v = ZSEG - 1; v > sgm; --v) X = fmad(sF[v][lane], X, sB[v][lane]);
+    if (col)
+        for (int c = c1 - 1; c >= c0; --c) {
+            zc[c * st + Nr + i] = X;
+            X = fmad(chb[c * 4 + 1], X, fmad(chb[c * 4 + 2], zc[c * st + i], zs[c * st + Nr + i]));
+        }
 }
 
 // Pass 3: solve every (column, chunk) from its carries.  Shared memory holds
 // the forward results of each warp: [warps][Rc][32*V] reals.
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(64) zsolve_kernel(const real *__restrict__ th, real *__restrict__ out,
+__global__ void __launch_bounds__(64, 8) zsolve_kernel(const real *__restrict__ th, real *__restrict__ out,
                                                     real *__restrict__ rho_out, const real *__restrict__ rho_in,
-                                                    int Nr, int Nz, int Rc, const int *__restrict__ rowcls,
+                                                    int Nr, int Nz, int Rc, const int *__restrict__ ucls,
+                                                    const int *__restrict__ rowcls,
                                                     const int *__restrict__ colcls, const real *__restrict__ pkA,
                                                     const real *__restrict__ pkB, LineTab<real> R, LineTab64 R64,
                                                     LineTab64 Z64, BcVals bc, const real *__restrict__ zc)
@@ -858,9 +918,10 @@ __global__ void __launch_bounds__(64) zsolve_kernel(const real *__restrict__ th,
     if (grp * COLS >= Nr) return;  // whole warp past the field (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
-    real *dsm = reinterpret_cast<real *>(smem_raw) + (size_t)w * Rc * COLS + lane * V;
+    real *dsm = reinterpret_cast<real *>(smem_raw) + (size_t)w * Rc * (COLS + 8) + lane * V;
     ZLane<real, V, MODE> L;
     L.init(th, colcls, pkA, pkB, Nr, Nz, grp * COLS + lane * V, lane, bc);
+    L.stage(reinterpret_cast<real *>(smem_raw) + (size_t)w * Rc * (COLS + 8) + (size_t)Rc * COLS, j0, j1);
     real dp[V], x[V], cin[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
@@ -869,43 +930,55 @@ __global__ void __launch_bounds__(64) zsolve_kernel(const real *__restrict__ th,
         x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + L.ib + q] : real(0);
         dp[q] = cin[q];
     }
-    z_walk<real, V, MODE>(L, rho_in, j0, j1, rowcls, R, [&](int j, const real(&d)[V], const real(&eA)[V][4], const real(&)[V][4]) {
+    z_walk<real, V, MODE>(L, rho_in, j0, j1, ucls[c], rowcls, R, [&](int j, const real(&d)[V], const real(&e)[V][8]) {
 #pragma unroll
-        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], eA[q][0], eA[q][1] * dp[q]);
+        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[q][0], e[q][1] * dp[q]);
         VecIO<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
     });
-    // backward from the carry-out, writing the solution rows
-    for (int j = j1 - 1; j >= j0; --j) {
-        real dd[V];
-        {
-            const real *p = dsm + (size_t)(j - j0) * COLS;
+    // backward from the carry-out, writing the solution rows; the rows added
+    // to the increments are loaded ZP at a time
+    for (int jt = j1 - 1; jt >= j0; jt -= ZP) {
+        real base[ZP][V];
+        if constexpr (MODE != MODE_LIT) {
 #pragma unroll
-            for (int q = 0; q < V; ++q) dd[q] = p[q];
+            for (int p = 0; p < ZP; ++p) {
+                const int j = jt - p;
+                L.row(MODE == MODE_CORR ? out : th, j >= j0 ? j : j0, base[p]);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const real cpq = (L.uni ? L.pa[0] : L.pa[q])[4 * j + 2];
-            x[q] = fmad(cpq, x[q], dd[q]);
-        }
-        if constexpr (MODE == MODE_REFINE) VecIO<real, V>::st(dsm + (size_t)(j - j0) * COLS, x);
-        if (!L.any) continue;
-        real o[V];
-        if constexpr (MODE == MODE_LIT) {
+        for (int p = 0; p < ZP; ++p) {
+            const int j = jt - p;
+            if (j < j0) break;
+            real dd[V], cpv[V];
+            {
+                const real *ps = dsm + (size_t)(j - j0) * COLS;
 #pragma unroll
-            for (int q = 0; q < V; ++q) o[q] = x[q];
-        } else {
-            real base[V];
-            L.row(MODE == MODE_CORR ? out : th, j, base);
+                for (int q = 0; q < V; ++q) dd[q] = ps[q];
+            }
+            if (L.allstg) {
+                const real c2 = L.stg[(j - L.jst) * 8 + 2];
 #pragma unroll
-            for (int q = 0; q < V; ++q) o[q] = base[q] + x[q];
-        }
-        real *orow = out + (size_t)j * Nr + L.ib;
-        if (L.vec) {
-            VecIO<real, V>::st(orow, o);
-        } else {
+                for (int q = 0; q < V; ++q) cpv[q] = c2;
+            } else {
 #pragma unroll
-            for (int q = 0; q < V; ++q)
-                if (L.ib + q < Nr) orow[q] = o[q];
+                for (int q = 0; q < V; ++q) cpv[q] = L.tA(q, j, 2);
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) x[q] = fmad(cpv[q], x[q], dd[q]);
+            if constexpr (MODE == MODE_REFINE) VecIO<real, V>::st(dsm + (size_t)(j - j0) * COLS, x);
+            if (!L.any) continue;
+            real o[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) o[q] = MODE == MODE_LIT ? x[q] : base[p][q] + x[q];
+            real *orow = out + (size_t)j * Nr + L.ib;
+            if (L.vec) {
+                VecIO<real, V>::st(orow, o);
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    if (L.ib + q < Nr) orow[q] = o[q];
+            }
         }
     }
 
@@ -919,8 +992,7 @@ __global__ void __launch_bounds__(64) zsolve_kernel(const real *__restrict__ th,
         for (int q = 0; q < V; ++q) {
             const bool in = ib + q < Nr;
             const real x0 = dsm[q];
-            xlo[q] = (j0 > 0 && in) ? (double)cin[q] + (double)(L.uni ? L.pa[0] : L.pa[q])[4 * (j0 - 1) + 2] * (double)x0
-                                    : 0.0;
+            xlo[q] = (j0 > 0 && in) ? (double)cin[q] + (double)L.pa[q][4 * (j0 - 1) + 2] * (double)x0 : 0.0;
             xhi[q] = (j1 < Nz && in) ? (double)zc[((size_t)c * 2 + 1) * Nr + ib + q] : 0.0;
         }
         double tm[V], t[V], tp[V];
@@ -1176,19 +1248,19 @@ static cudaError_t zsweep_pass(const heat_ctx *ctx, const real *in, real *out, r
     {
         constexpr int WPB = 4;
         const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
-        zsum_kernel<real, V, MODE><<<grid, 32 * WPB, 0, ctx->stream>>>(in, rho_in, Nr, Nz, Rc, ctx->d_rowcls,
-                                                                      ctx->d_colcls, pkA, pkB, R, bc_vals(ctx), zs);
+        zsum_kernel<real, V, MODE><<<grid, 32 * WPB, (size_t)WPB * Rc * 8 * sizeof(real), ctx->stream>>>(
+            in, rho_in, Nr, Nz, Rc, ctx->zp.ucls, ctx->d_rowcls, ctx->d_colcls, pkA, pkB, R, bc_vals(ctx), zs);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    zcarry_kernel<real><<<(Nr + 7) / 8, 256, 0, ctx->stream>>>(Nr, nch, ctx->d_colcls, ZBufs<real>::ch(ctx), zs, zc);
+    zcarry_kernel<real><<<(Nr + 31) / 32, 32 * ZSEG, 0, ctx->stream>>>(Nr, nch, ctx->d_colcls, ZBufs<real>::ch(ctx), zs, zc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int WPB = (size_t)Rc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
     const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
     auto kern = zsolve_kernel<real, V, MODE>;
-    const size_t smem = (size_t)WPB * Rc * COLS * sizeof(real);
+    const size_t smem = (size_t)WPB * Rc * (COLS + 8) * sizeof(real);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    kern<<<grid, 32 * WPB, smem, ctx->stream>>>(in, out, rho_out, rho_in, Nr, Nz, Rc, ctx->d_rowcls, ctx->d_colcls, pkA,
+    kern<<<grid, 32 * WPB, smem, ctx->stream>>>(in, out, rho_out, rho_in, Nr, Nz, Rc, ctx->zp.ucls, ctx->d_rowcls, ctx->d_colcls, pkA,
                                                 pkB, R, ctx->dR.full, ctx->dZ.full, bc_vals(ctx), zc);
     return cudaGetLastError();
 }
