@@ -54,6 +54,7 @@ extern "C" {
 #define HEAT_ERR_NONFINITE (-3) /* the field holds NaN or Inf (found by heat_energy) */
 #define HEAT_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up               */
 #define HEAT_ERR_OOM (-5)       /* device allocation failed                         */
+#define HEAT_ERR_TOO_LARGE (-6) /* size beyond a fixed capacity (heat_energy_noalloc) */
 
 /* ---- precision of the stored field and the line solves ---- */
 #define HEAT_FP64 0             /* FP64 field, FP64 line solves                     */
@@ -150,6 +151,27 @@ int heat_set_field(heat_ctx *ctx, const double *in, size_t n, int on_device);
  *   E(next) - E(now) = tau Q + (tau/2) (Phi(now) + Phi(next)).
  * Any pointer may be NULL.  Returns HEAT_ERR_NONFINITE if E or Phi is not finite. */
 int heat_energy(heat_ctx *ctx, double *E, double *Phi, double *Q);
+
+/* Same results as heat_energy (to rounding: the partial sums are grouped per
+ * grid row instead of per block), but the call allocates no device memory and
+ * uses none of the context's scratch: its partial sums live in a fixed
+ * file-scope device array of 2 * HEAT_NOALLOC_MAX_ROWS + 2 doubles (128 KB),
+ * one per process and device.  The paper has no counterpart; this exists for
+ * callers that must not allocate at the point they ask for the heat balance
+ * (a monitor under a hard device-memory budget, or one auditing a context
+ * whose scratch it cannot assume idle).
+ *   ctx: a live context; its device must be current.  Synchronizes ctx's stream.
+ *   E, Phi, Q: as heat_energy; any may be NULL.
+ * Returns HEAT_ERR_TOO_LARGE if Nz > HEAT_NOALLOC_MAX_ROWS, HEAT_ERR_ARG for a
+ * NULL ctx, HEAT_ERR_CUDA if a CUDA call fails, HEAT_ERR_NONFINITE as heat_energy.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and must come before any stream capture on that
+ * device.  The array keeps the last call's contents; a call rewrites every slot
+ * it reads.  Calls through this entry point are serialised by a process-wide
+ * lock and each drains its stream before returning, because overlapping calls
+ * would race on the one array.  No claim is made for use inside a CUDA graph. */
+#define HEAT_NOALLOC_MAX_ROWS 8192
+int heat_energy_noalloc(heat_ctx *ctx, double *E, double *Phi, double *Q);
 
 /* Grid and limits.  Any pointer may be NULL; r_centres holds Nr, z_centres Nz
  * doubles.  tau_exp = min over active cells of C / (sum of the cell's

@@ -158,6 +158,7 @@ const char *heat_strerror(int status)
     case HEAT_ERR_NONFINITE: return "non-finite field";
     case HEAT_ERR_TIMEOUT: return "device wait timed out";
     case HEAT_ERR_OOM: return "device out of memory";
+    case HEAT_ERR_TOO_LARGE: return "size beyond a fixed capacity";
     default: return "unknown status";
     }
 }

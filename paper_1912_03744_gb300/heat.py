@@ -16,13 +16,14 @@ LIB_PATH = os.path.join(_PKG, "libheat.so")
 
 HEAT_OK = 0
 STATUS = {0: "ok", -1: "HEAT_ERR_ARG", -2: "HEAT_ERR_CUDA", -3: "HEAT_ERR_NONFINITE",
-          -4: "HEAT_ERR_TIMEOUT", -5: "HEAT_ERR_OOM"}
+          -4: "HEAT_ERR_TIMEOUT", -5: "HEAT_ERR_OOM", -6: "HEAT_ERR_TOO_LARGE"}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 NUMPY_DTYPE = {"fp64": np.float64, "fp32": np.float32, "fp32_refined": np.float32}
 
 # Every extern "C" symbol include/heat.h declares.
 SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field", "heat_set_field", "heat_energy",
-           "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror"]
+           "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror",
+           "heat_energy_noalloc"]
 
 
 class HeatError(RuntimeError):
@@ -74,6 +75,7 @@ def load():
         L.heat_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.heat_set_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.heat_energy.argtypes = [vp, dp, dp, dp]
+        L.heat_energy_noalloc.argtypes = [vp, dp, dp, dp]
         L.heat_info.argtypes = [vp, ip, ip, dp, dp, dp]
         L.heat_launches_per_step.argtypes = [vp]
         L.heat_sync.argtypes = [vp]
@@ -198,6 +200,14 @@ class HeatSolver:
         """(E, Phi, Q) in FP64 (see include/heat.h)."""
         e, f, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check("heat_energy", load().heat_energy(self._h, ctypes.byref(e), ctypes.byref(f), ctypes.byref(q)))
+        return e.value, f.value, q.value
+
+    def energy_noalloc(self):
+        """(E, Phi, Q) like energy(), computed with no device allocation and
+        none of the context's scratch (include/heat.h)."""
+        e, f, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check("heat_energy_noalloc",
+               load().heat_energy_noalloc(self._h, ctypes.byref(e), ctypes.byref(f), ctypes.byref(q)))
         return e.value, f.value, q.value
 
     def centres(self):
