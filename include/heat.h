@@ -187,6 +187,59 @@ int heat_sync(heat_ctx *ctx);
 
 void heat_destroy(heat_ctx *ctx);
 
+/* ---- batched ensemble ----
+ * n independent problems of one precision and face mean, each on its own
+ * grid with its own materials and dt, advanced in lockstep (the ensemble of
+ * parameter variations the paper's method is run over, Sec. 5).  Each member
+ * is an ordinary context; every stage of a step is one kernel launch over all
+ * members (member index = a grid dimension), and heat_batch_step replays CUDA
+ * graphs of whole steps.  Results per member are those of a single context
+ * up to rounding (the batch may cut r-lines into different per-thread chunks).
+ * Member limit: Nr <= HEAT_BATCH_MAX_NR (one r-line within one warp). */
+typedef struct heat_batch heat_batch;
+#define HEAT_BATCH_MAX_NR 1024
+
+/* geoms[n], mats[n], dts[n]: per-member arguments as heat_create; opt shared.
+ * stream: the caller's stream (NULL = legacy default stream); heat_batch_step
+ * work is ordered after work already queued there, and work queued there
+ * afterwards is ordered after the steps.  The batch runs on a stream of its
+ * own (graph capture needs one).  1 <= n <= 65535.  Allocates every member's
+ * device buffers; HEAT_ERR_ARG on bad sizes, HEAT_ERR_OOM, HEAT_ERR_CUDA. */
+int heat_batch_create(int n, const heat_geometry *geoms, const heat_materials *mats,
+                      const heat_options *opt, const double *dts, void *stream,
+                      heat_batch **out);
+
+/* Borrow member i's context for heat_field, heat_set_field, heat_energy,
+ * heat_info (and heat_step of that member alone).  The batch owns it:
+ * heat_destroy on it does nothing, heat_sweep and heat_set_dt return
+ * HEAT_ERR_ARG.  Its stream is the batch's stream. */
+int heat_batch_member(heat_batch *b, int i, heat_ctx **ctx);
+
+/* Enqueue n >= 0 full steps of every member (asynchronous). */
+int heat_batch_step(heat_batch *b, int n);
+
+/* Wait for the batch stream. */
+int heat_batch_sync(heat_batch *b);
+
+/* Autotuner: time every valid schedule (r-sweep cells per thread K, rows
+ * per line slot, z-solve warps per block) for trial_steps (1..1000) steps
+ * each, on the members' current fields, and keep the fastest.  The members'
+ * fields are saved before and restored after, so the state does not change.
+ * Allocates one temporary copy of all fields.  best_ms (may be NULL):
+ * the winner's device time per step. */
+int heat_batch_tune(heat_batch *b, int trial_steps, double *best_ms);
+
+/* Set or read the schedule: rK in {0 (default), 4, 8, 16, 32}, band >= 0
+ * (0 = default), zwpb in {0 (default), 1, 2}.  An invalid combination for
+ * these members returns HEAT_ERR_ARG and keeps the current schedule. */
+int heat_batch_set_tuning(heat_batch *b, int rK, int band, int zwpb);
+int heat_batch_get_tuning(heat_batch *b, int *rK, int *band, int *zwpb);
+
+/* Kernel launches one batch step enqueues (independent of n). */
+int heat_batch_launches_per_step(heat_batch *b);
+
+void heat_batch_destroy(heat_batch *b);
+
 const char *heat_strerror(int status);
 
 #ifdef __cplusplus

@@ -3,6 +3,8 @@
 // of every step is computed by the kernels in heat_sweeps.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -18,6 +20,7 @@ void build_zpartition(heat_ctx *);
 cudaError_t launch_fill(heat_ctx *, int, double);
 cudaError_t launch_steps(heat_ctx *, int);
 cudaError_t launch_sweep(heat_ctx *, int);
+cudaError_t ctx_plan(heat_ctx *);
 cudaError_t launch_energy(heat_ctx *);
 cudaError_t launch_theta_to_T(heat_ctx *, double *);
 cudaError_t launch_T_to_theta(heat_ctx *, const double *);
@@ -32,6 +35,7 @@ namespace {
 int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return HEAT_OK;
+    if (std::getenv("HEAT_DEBUG")) std::fprintf(stderr, "libheat: %s\n", cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return HEAT_ERR_OOM;
     return HEAT_ERR_CUDA;
 }
@@ -137,7 +141,8 @@ void free_ctx(heat_ctx *ctx)
     void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32,   ctx->dZ.buf64,   ctx->dZ.buf32, ctx->d_rowcls,
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
-                    ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls};
+                    ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,
+                    ctx->d_args};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -226,6 +231,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     // uniform initial field T = T_init (eq. "initcond"), stored as T - T_ref
     HEAT_TRY(launch_fill(ctx, 0, mat->T_init - ctx->T_ref));
     HEAT_TRY(launch_fill(ctx, 1, mat->T_init - ctx->T_ref));
+    HEAT_TRY(ctx_plan(ctx));
     HEAT_TRY(cudaStreamSynchronize(ctx->stream));
 #undef HEAT_TRY
     *out = ctx;
@@ -234,7 +240,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
 
 int heat_set_dt(heat_ctx *ctx, double dt)
 {
-    if (!ctx || !(dt > 0.0) || !std::isfinite(dt)) return HEAT_ERR_ARG;
+    if (!ctx || !(dt > 0.0) || !std::isfinite(dt) || ctx->batch_member) return HEAT_ERR_ARG;
     HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
     ctx->tau = dt;
     build_tables(ctx);
@@ -242,12 +248,13 @@ int heat_set_dt(heat_ctx *ctx, double dt)
     int st = upload_tab(ctx, ctx->R, ctx->dR);
     if (st != HEAT_OK) return st;
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
-    return upload_zpart(ctx);
+    if ((st = upload_zpart(ctx)) != HEAT_OK) return st;
+    return cuda_status(ctx_plan(ctx));
 }
 
 int heat_sweep(heat_ctx *ctx, int dir)
 {
-    if (!ctx || (dir != 0 && dir != 1)) return HEAT_ERR_ARG;
+    if (!ctx || (dir != 0 && dir != 1) || ctx->batch_member) return HEAT_ERR_ARG;
     if ((dir == 1) != (ctx->half == 1)) return HEAT_ERR_ARG;
     int st = cuda_status(launch_sweep(ctx, dir));
     if (st != HEAT_OK) return st;
@@ -342,7 +349,7 @@ int heat_sync(heat_ctx *ctx)
 
 void heat_destroy(heat_ctx *ctx)
 {
-    if (!ctx) return;
+    if (!ctx || ctx->batch_member) return;
     cudaStreamSynchronize(ctx->stream);
     free_ctx(ctx);
 }

@@ -56,6 +56,52 @@ struct LineTab64 {
     const double *cap, *dsum, *dbc;
 };
 
+// theta_bc of the faces r_lo, r_hi, z_lo, z_hi
+struct BcVals {
+    double th[4];
+};
+
+// Everything a sweep kernel needs about one problem instance.  Kernels take
+// a device array of these and pick their instance from a grid index, so one
+// launch serves one problem or a whole batch.  The field ping-pongs between
+// f0 and f1: with flip = 0 a sweep reads f0 and writes f1, with flip = 1 the
+// reverse.
+template <typename real>
+struct SweepArgs {
+    int Nr, Nz;
+    int G, band;              // r-sweep: threads per line, rows per line slot
+    int Rc, nch;              // z partition
+    const int *rowcls, *colcls;
+    LineTab<real> R, Z;
+    LineTab64 R64, Z64;
+    BcVals bc;
+    const real *pkA, *pkB, *chk;
+    const int *ucls;
+    real *zs, *zc, *rho;
+    real *f0, *f1;
+};
+
+// One kernel launch of a sweep.  Every sweep kernel takes a device array of
+// SweepArgs, and all but the carry pass also the flip flag.
+struct Launch {
+    const void *fn = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+    bool flip = false;
+};
+
+// Launch schedule of both half-steps for one set of instances (one problem,
+// or a batch sharing precision), with the tunables it was built from.
+struct Tuning {
+    int rK = 0;    // r-sweep cells per thread (4, 8, 16, 32); 0 = default rule
+    int band = 0;  // r-sweep consecutive rows per line slot; 0 = default rule
+    int zwpb = 0;  // z-solve warps per block (1 or 2); 0 = default rule
+};
+struct SweepPlan {
+    std::vector<Launch> dir[2];
+    Tuning used;   // the values the plan resolved to
+};
+
 // Host FP64 master of one direction's tables.
 struct HostTab {
     int n_class = 0, N = 0;
@@ -151,4 +197,9 @@ struct heat_ctx {
     double *d_tmp64 = nullptr;    // Nr*Nz doubles for host/device transfers of FP32 fields
     int n_part = 0;
     int deferred = HEAT_OK;
+    // launch plan of one sweep direction and its device argument block
+    heat::SweepPlan plan;
+    std::vector<unsigned char> h_args;  // one SweepArgs<real>
+    void *d_args = nullptr;
+    bool batch_member = false;          // owned by a heat_batch (no heat_sweep / heat_destroy)
 };

@@ -52,11 +52,6 @@ namespace heat {
 
 enum { MODE_LIT = 0, MODE_DELTA = 1, MODE_REFINE = 2, MODE_CORR = 3 };
 
-// theta_bc of the faces r_lo, r_hi, z_lo, z_hi
-struct BcVals {
-    double th[4];
-};
-
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
@@ -259,11 +254,18 @@ __device__ __forceinline__ void solve_row(real (&d)[K], const real (&inv)[K], co
 // NRING = 0 selects direct global loads of rows j-1, j, j+1 (rows too long
 // for a ring in shared memory).
 template <typename real, int K, int MODE, int LB, int NRING>
-__global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const real *__restrict__ th, real *__restrict__ out, int Nr,
-                                                    int Nz, int G, int band, const int *__restrict__ rowcls,
-                                                    const int *__restrict__ colcls, LineTab<real> R, LineTab<real> Z,
-                                                    LineTab64 R64, LineTab64 Z64, BcVals bc)
+__global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    const SweepArgs<real> &A = args[blockIdx.y];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    real *__restrict__ out = flip ? A.f0 : A.f1;
+    const int Nr = A.Nr, Nz = A.Nz, G = A.G, band = A.band;
+    const int *__restrict__ rowcls = A.rowcls;
+    const int *__restrict__ colcls = A.colcls;
+    const LineTab<real> &R = A.R, &Z = A.Z;
+    const LineTab64 &R64 = A.R64, &Z64 = A.Z64;
+    const BcVals bc = A.bc;
+    if ((int)blockIdx.x * (int)(blockDim.x / G) * band >= Nz) return;  // past this instance (block-uniform)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ real sA[32], sB[32], sC[32];
     __shared__ double sLo[32], sHi[32];
@@ -800,13 +802,21 @@ __device__ __forceinline__ void z_walk(ZLane<real, V, MODE> &L, const real *__re
 // Pass 1: summaries B = sum r wB and G0 = sum r wG of every (column, chunk):
 // zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks).
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(128, 4) zsum_kernel(const real *__restrict__ th, const real *__restrict__ rho, int Nr,
-                                                   int Nz, int Rc, const int *__restrict__ ucls,
-                                                   const int *__restrict__ rowcls,
-                                                   const int *__restrict__ colcls, const real *__restrict__ pkA,
-                                                   const real *__restrict__ pkB, LineTab<real> R, BcVals bc,
-                                                   real *__restrict__ zs)
+__global__ void __launch_bounds__(128, 4) zsum_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    const SweepArgs<real> &A = args[blockIdx.z];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    const real *__restrict__ rho = MODE == MODE_CORR ? A.rho : nullptr;
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
+    if ((int)blockIdx.y >= A.nch) return;
+    const int *__restrict__ ucls = A.ucls;
+    const int *__restrict__ rowcls = A.rowcls;
+    const int *__restrict__ colcls = A.colcls;
+    const real *__restrict__ pkA = A.pkA;
+    const real *__restrict__ pkB = A.pkB;
+    const LineTab<real> &R = A.R;
+    const BcVals bc = A.bc;
+    real *__restrict__ zs = A.zs;
     const int lane = threadIdx.x & 31;
     const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
@@ -850,10 +860,15 @@ __global__ void __launch_bounds__(128, 4) zsum_kernel(const real *__restrict__ t
 constexpr int ZSEG = 8;
 
 template <typename real>
-__global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(int Nr, int nch, const int *__restrict__ colcls,
-                                                           const real *__restrict__ chk, const real *__restrict__ zs,
-                                                           real *__restrict__ zc)
+__global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(const SweepArgs<real> *__restrict__ args)
 {
+    const SweepArgs<real> &A = args[blockIdx.y];
+    const int Nr = A.Nr, nch = A.nch;
+    if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
+    const int *__restrict__ colcls = A.colcls;
+    const real *__restrict__ chk = A.chk;
+    const real *__restrict__ zs = A.zs;
+    real *__restrict__ zc = A.zc;
     __shared__ real sF[ZSEG][32], sB[ZSEG][32];
     const int lane = threadIdx.x & 31, sgm = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
@@ -903,14 +918,24 @@ __global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(int Nr, int nch, cons
 // Pass 3: solve every (column, chunk) from its carries.  Shared memory holds
 // the forward results of each warp: [warps][Rc][32*V] reals.
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(64, 8) zsolve_kernel(const real *__restrict__ th, real *__restrict__ out,
-                                                    real *__restrict__ rho_out, const real *__restrict__ rho_in,
-                                                    int Nr, int Nz, int Rc, const int *__restrict__ ucls,
-                                                    const int *__restrict__ rowcls,
-                                                    const int *__restrict__ colcls, const real *__restrict__ pkA,
-                                                    const real *__restrict__ pkB, LineTab<real> R, LineTab64 R64,
-                                                    LineTab64 Z64, BcVals bc, const real *__restrict__ zc)
+__global__ void __launch_bounds__(64, 8) zsolve_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    const SweepArgs<real> &A = args[blockIdx.z];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    real *__restrict__ out = flip ? A.f0 : A.f1;
+    real *__restrict__ rho_out = MODE == MODE_REFINE ? A.rho : nullptr;
+    const real *__restrict__ rho_in = MODE == MODE_CORR ? A.rho : nullptr;
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
+    if ((int)blockIdx.y >= A.nch) return;
+    const int *__restrict__ ucls = A.ucls;
+    const int *__restrict__ rowcls = A.rowcls;
+    const int *__restrict__ colcls = A.colcls;
+    const real *__restrict__ pkA = A.pkA;
+    const real *__restrict__ pkB = A.pkB;
+    const LineTab<real> &R = A.R;
+    const LineTab64 &R64 = A.R64, &Z64 = A.Z64;
+    const BcVals bc = A.bc;
+    const real *__restrict__ zc = A.zc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int COLS = 32 * V;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1161,133 +1186,192 @@ static int next_pow2(int x)
     return p;
 }
 
-static BcVals bc_vals(const heat_ctx *ctx)
+// Cells per thread of the r-sweep for lines of up to Nr cells.
+static int default_rK(int word, int Nr)
 {
-    BcVals b;
-    for (int f = 0; f < 4; ++f) b.th[f] = ctx->theta_bc[f];
-    return b;
+    if (word == 8 && Nr <= 1024) return 4;
+    if (Nr <= 8192) return 8;
+    if (Nr <= 16384) return 16;
+    return 32;
 }
 
-template <typename real>
-struct ZBufs;
-template <>
-struct ZBufs<float> {
-    static const float *pk(const heat_ctx *c) { return c->zp.pk32; }
-    static const float *ch(const heat_ctx *c) { return c->zp.ch32; }
-    static float *sum(const heat_ctx *c) { return c->d_zsum; }
-};
-template <>
-struct ZBufs<double> {
-    static const double *pk(const heat_ctx *c) { return c->zp.pk64; }
-    static const double *ch(const heat_ctx *c) { return c->zp.ch64; }
-    static double *sum(const heat_ctx *c) { return c->d_zsum64; }
-};
-
-template <typename real, int K, int MODE>
-static cudaError_t rsweep_k(const heat_ctx *ctx, const real *in, real *out, const LineTab<real> &R,
-                            const LineTab<real> &Z)
+static cudaError_t allow_smem(const void *fn, size_t smem)
 {
-    const int Nr = ctx->g.Nr, Nz = ctx->g.Nz;
-    const int G = next_pow2((Nr + K - 1) / K);
-    const int block = G <= 32 ? 128 : G;
-    const int lpb = block / G;
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    const int maxdyn = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in maximum
+    if (smem > (size_t)maxdyn) return cudaErrorInvalidValue;
+    // The attribute only raises a per-kernel ceiling; setting it to the device
+    // maximum keeps every plan's launches valid whichever plan was made last.
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
+}
+
+// r-sweep launch for n instances, all sharing K: instance m runs in grid row
+// blockIdx.y = m with G_m threads per line and lpb_m = block / G_m lines per
+// block, each line slot walking band_m consecutive rows.  A batch (n > 1)
+// keeps every line inside one warp (G <= 32), so the block size is uniform.
+template <typename real, int K, int MODE>
+static cudaError_t plan_rsweep_k(SweepArgs<real> *h, int n, int band_req, Launch &L)
+{
+    int Gmax = 1;
+    for (int m = 0; m < n; ++m) {
+        h[m].G = next_pow2((h[m].Nr + K - 1) / K);
+        Gmax = h[m].G > Gmax ? h[m].G : Gmax;
+    }
+    if (n > 1 && Gmax > 32) return cudaErrorInvalidValue;
+    const int block = Gmax <= 32 ? 128 : Gmax;
     // deepest ring that fits: 8 rows, else 4, else direct loads
-    const size_t row_bytes = (size_t)lpb * G * K * sizeof(real);
+    const size_t row_bytes = (size_t)block * K * sizeof(real);
     const size_t budget = 200 * 1024;
     const int nring = 8 * row_bytes <= budget ? 8 : (4 * row_bytes <= budget ? 4 : 0);
     const size_t smem = nring * row_bytes;
     int per_sm = smem ? (int)(budget / (smem + 4096)) : 4;
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-    const int slots_wanted = kSMs * per_sm * lpb;
-    const int slots = Nz < slots_wanted ? Nz : slots_wanted;
-    const int band = (Nz + slots - 1) / slots;
-    const int grid = ((Nz + band - 1) / band + lpb - 1) / lpb;
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, block, smem, ctx->stream>>>(in, out, Nr, Nz, G, band, ctx->d_rowcls, ctx->d_colcls, R, Z,
-                                                 ctx->dR.full, ctx->dZ.full, bc_vals(ctx));
-        return cudaGetLastError();
+    // rows per slot: the largest band (<= 64) that still gives two waves of
+    // resident blocks over all instances, or one row per slot if none does
+    auto blocks_for = [&](int band) {
+        long long tot = 0;
+        for (int m = 0; m < n; ++m) {
+            const int lpb = block / h[m].G;
+            tot += ((h[m].Nz + band - 1) / band + lpb - 1) / lpb;
+        }
+        return tot;
     };
-    if (block <= 256) {
-        if (nring == 8) return go(rsweep_kernel<real, K, MODE, 256, 8>);
-        if (nring == 4) return go(rsweep_kernel<real, K, MODE, 256, 4>);
-        return go(rsweep_kernel<real, K, MODE, 256, 0>);
+    int band = band_req;
+    if (band <= 0) {
+        if (n == 1) {
+            const int lpb = block / h[0].G;
+            const int slots_wanted = kSMs * per_sm * lpb;
+            const int slots = h[0].Nz < slots_wanted ? h[0].Nz : slots_wanted;
+            band = (h[0].Nz + slots - 1) / slots;
+        } else {
+            band = 1;
+            for (int b = 64; b > 1; b >>= 1)
+                if (blocks_for(b) >= 2LL * kSMs * per_sm) { band = b; break; }
+        }
     }
-    if (nring == 8) return go(rsweep_kernel<real, K, MODE, 1024, 8>);
-    if (nring == 4) return go(rsweep_kernel<real, K, MODE, 1024, 4>);
-    return go(rsweep_kernel<real, K, MODE, 1024, 0>);
+    int gx = 1;
+    for (int m = 0; m < n; ++m) {
+        h[m].band = band;
+        const int lpb = block / h[m].G;
+        const int bx = ((h[m].Nz + band - 1) / band + lpb - 1) / lpb;
+        gx = bx > gx ? bx : gx;
+    }
+    const void *fn;
+    if (block <= 256)
+        fn = nring == 8 ? (const void *)rsweep_kernel<real, K, MODE, 256, 8>
+                        : nring == 4 ? (const void *)rsweep_kernel<real, K, MODE, 256, 4>
+                                     : (const void *)rsweep_kernel<real, K, MODE, 256, 0>;
+    else
+        fn = nring == 8 ? (const void *)rsweep_kernel<real, K, MODE, 1024, 8>
+                        : nring == 4 ? (const void *)rsweep_kernel<real, K, MODE, 1024, 4>
+                                     : (const void *)rsweep_kernel<real, K, MODE, 1024, 0>;
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    L.fn = fn;
+    L.grid = dim3(gx, n, 1);
+    L.block = dim3(block, 1, 1);
+    L.smem = smem;
+    L.flip = true;
+    return cudaSuccess;
 }
 
 template <typename real, int MODE>
-static cudaError_t launch_rsweep(const heat_ctx *ctx, const real *in, real *out, const LineTab<real> &R,
-                                 const LineTab<real> &Z)
+static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
-    const int Nr = ctx->g.Nr;
-    if (sizeof(real) == 8 && Nr <= 1024) return rsweep_k<real, 4, MODE>(ctx, in, out, R, Z);
-    if (Nr <= 8192) return rsweep_k<real, 8, MODE>(ctx, in, out, R, Z);
-    if (Nr <= 16384) return rsweep_k<real, 16, MODE>(ctx, in, out, R, Z);
-    return rsweep_k<real, 32, MODE>(ctx, in, out, R, Z);
+    int maxNr = 0;
+    for (int m = 0; m < n; ++m) maxNr = h[m].Nr > maxNr ? h[m].Nr : maxNr;
+    int K = tu.rK;
+    if (K <= 0) {
+        K = default_rK((int)sizeof(real), maxNr);
+        if (n > 1)
+            while (K < 32 && (maxNr + K - 1) / K > 32) K *= 2;
+    }
+    tu.rK = K;
+    cudaError_t e;
+    switch (K) {
+    case 4: e = plan_rsweep_k<real, 4, MODE>(h, n, tu.band, L); break;
+    case 8: e = plan_rsweep_k<real, 8, MODE>(h, n, tu.band, L); break;
+    case 16: e = plan_rsweep_k<real, 16, MODE>(h, n, tu.band, L); break;
+    case 32: e = plan_rsweep_k<real, 32, MODE>(h, n, tu.band, L); break;
+    default: return cudaErrorInvalidValue;
+    }
+    tu.band = h[0].band;
+    return e;
 }
 
+// One z pass: chunk summaries, carries, chunk solves, for n instances
+// (instance m in the last grid dimension; blocks past an instance's columns
+// or chunks return at once).
 template <typename real, int MODE>
-static cudaError_t zsweep_pass(const heat_ctx *ctx, const real *in, real *out, real *rho_out, const real *rho_in,
-                               const LineTab<real> &R, const LineTab<real> &)
+static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::vector<Launch> &out)
 {
     constexpr int V = 16 / (int)sizeof(real);
     constexpr int COLS = 32 * V;
-    const int Nr = ctx->g.Nr, Nz = ctx->g.Nz;
-    const int Rc = ctx->zp.Rc, nch = ctx->zp.n_chunks;
-    const int groups = (Nr + COLS - 1) / COLS;
-    const real *pk = ZBufs<real>::pk(ctx);
-    const size_t npk = (size_t)ctx->Z.n_class * Nz;
-    const real *pkA = pk, *pkB = pk + 4 * npk;
-    real *zs = ZBufs<real>::sum(ctx);
-    real *zc = zs + (size_t)2 * nch * Nr;
-    cudaError_t e;
-    {
-        constexpr int WPB = 4;
-        const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
-        zsum_kernel<real, V, MODE><<<grid, 32 * WPB, (size_t)WPB * Rc * 8 * sizeof(real), ctx->stream>>>(
-            in, rho_in, Nr, Nz, Rc, ctx->zp.ucls, ctx->d_rowcls, ctx->d_colcls, pkA, pkB, R, bc_vals(ctx), zs);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int maxNr = 0, maxRc = 0, maxNch = 0;
+    for (int m = 0; m < n; ++m) {
+        maxNr = h[m].Nr > maxNr ? h[m].Nr : maxNr;
+        maxRc = h[m].Rc > maxRc ? h[m].Rc : maxRc;
+        maxNch = h[m].nch > maxNch ? h[m].nch : maxNch;
     }
-    zcarry_kernel<real><<<(Nr + 31) / 32, 32 * ZSEG, 0, ctx->stream>>>(Nr, nch, ctx->d_colcls, ZBufs<real>::ch(ctx), zs, zc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int WPB = (size_t)Rc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
-    const dim3 grid((groups + WPB - 1) / WPB, nch, 1);
-    auto kern = zsolve_kernel<real, V, MODE>;
-    const size_t smem = (size_t)WPB * Rc * (COLS + 8) * sizeof(real);
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    kern<<<grid, 32 * WPB, smem, ctx->stream>>>(in, out, rho_out, rho_in, Nr, Nz, Rc, ctx->zp.ucls, ctx->d_rowcls, ctx->d_colcls, pkA,
-                                                pkB, R, ctx->dR.full, ctx->dZ.full, bc_vals(ctx), zc);
-    return cudaGetLastError();
+    const int groups = (maxNr + COLS - 1) / COLS;
+    Launch a, b, c;
+    constexpr int SWPB = 4;
+    a.fn = (const void *)zsum_kernel<real, V, MODE>;
+    a.grid = dim3((groups + SWPB - 1) / SWPB, maxNch, n);
+    a.block = dim3(32 * SWPB, 1, 1);
+    a.smem = (size_t)SWPB * maxRc * 8 * sizeof(real);
+    a.flip = true;
+    cudaError_t e = allow_smem(a.fn, a.smem);
+    if (e != cudaSuccess) return e;
+    b.fn = (const void *)zcarry_kernel<real>;
+    b.grid = dim3((maxNr + 31) / 32, n, 1);
+    b.block = dim3(32 * ZSEG, 1, 1);
+    b.smem = 0;
+    b.flip = false;
+    int wpb = tu.zwpb;
+    if (wpb != 1 && wpb != 2) wpb = (size_t)maxRc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
+    tu.zwpb = wpb;
+    c.fn = (const void *)zsolve_kernel<real, V, MODE>;
+    c.grid = dim3((groups + wpb - 1) / wpb, maxNch, n);
+    c.block = dim3(32 * wpb, 1, 1);
+    c.smem = (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
+    c.flip = true;
+    if ((e = allow_smem(c.fn, c.smem)) != cudaSuccess) return e;
+    out.push_back(a);
+    out.push_back(b);
+    out.push_back(c);
+    return cudaSuccess;
 }
 
+// The whole plan of one form.  Fills G and band of every h[m].
 template <typename real, int MODE>
-static cudaError_t launch_zsweep(const heat_ctx *ctx, const real *in, real *out, const LineTab<real> &R,
-                                 const LineTab<real> &Z)
+static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, SweepPlan &plan)
 {
+    plan = SweepPlan();
+    Tuning tu = req;
+    Launch r;
+    cudaError_t e = plan_rsweep<real, MODE>(h, n, tu, r);
+    if (e != cudaSuccess) return e;
+    plan.dir[0].push_back(r);
     if constexpr (MODE == MODE_REFINE) {
-        cudaError_t e = zsweep_pass<real, MODE_REFINE>(ctx, in, out, ctx->d_rho, nullptr, R, Z);
-        if (e != cudaSuccess) return e;
-        return zsweep_pass<real, MODE_CORR>(ctx, in, out, nullptr, ctx->d_rho, R, Z);
+        if ((e = plan_zpass<real, MODE_REFINE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+        if ((e = plan_zpass<real, MODE_CORR>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
     } else {
-        return zsweep_pass<real, MODE>(ctx, in, out, nullptr, nullptr, R, Z);
+        if ((e = plan_zpass<real, MODE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
     }
+    plan.used = tu;
+    return cudaSuccess;
 }
 
-template <typename real, int MODE>
-static cudaError_t sweep_mode(heat_ctx *ctx, int dir, const real *a, real *b, const LineTab<real> &R,
-                              const LineTab<real> &Z)
-{
-    return dir == 0 ? launch_rsweep<real, MODE>(ctx, a, b, R, Z) : launch_zsweep<real, MODE>(ctx, a, b, R, Z);
-}
-
-// Per-form entry points, each compiled in its own translation unit.
-cudaError_t sweep_fp64(heat_ctx *ctx, int dir, const void *a, void *b);
-cudaError_t sweep_fp32(heat_ctx *ctx, int dir, const void *a, void *b);
-cudaError_t sweep_fp32_refined(heat_ctx *ctx, int dir, const void *a, void *b);
+// Per-form plan builders, each compiled in its own translation unit.
+cudaError_t plan_fp64(SweepArgs<double> *h, int n, const Tuning &req, SweepPlan &plan);
+cudaError_t plan_fp32(SweepArgs<float> *h, int n, const Tuning &req, SweepPlan &plan);
+cudaError_t plan_fp32_refined(SweepArgs<float> *h, int n, const Tuning &req, SweepPlan &plan);
 
 }  // namespace heat

@@ -5,34 +5,125 @@
 
 namespace heat {
 
-// One half-step from buffer a into buffer b.
-cudaError_t launch_sweep_buffers(heat_ctx *ctx, int dir, const void *a, void *b)
+// Sweep arguments of one instance, from its context (host copy).
+template <typename real>
+static SweepArgs<real> make_args_t(const heat_ctx *ctx);
+
+template <>
+SweepArgs<float> make_args_t<float>(const heat_ctx *ctx)
 {
-    switch (ctx->precision) {
-    case HEAT_FP64: return sweep_fp64(ctx, dir, a, b);
-    case HEAT_FP32: return sweep_fp32(ctx, dir, a, b);
-    default: return sweep_fp32_refined(ctx, dir, a, b);
+    SweepArgs<float> a{};
+    a.R = ctx->dR.t32;
+    a.Z = ctx->dZ.t32;
+    const size_t npk = (size_t)ctx->Z.n_class * ctx->g.Nz;
+    a.pkA = ctx->zp.pk32;
+    a.pkB = ctx->zp.pk32 + 4 * npk;
+    a.chk = ctx->zp.ch32;
+    a.zs = ctx->d_zsum;
+    a.rho = ctx->d_rho;
+    return a;
+}
+
+template <>
+SweepArgs<double> make_args_t<double>(const heat_ctx *ctx)
+{
+    SweepArgs<double> a{};
+    a.R = ctx->dR.t64;
+    a.Z = ctx->dZ.t64;
+    const size_t npk = (size_t)ctx->Z.n_class * ctx->g.Nz;
+    a.pkA = ctx->zp.pk64;
+    a.pkB = ctx->zp.pk64 + 4 * npk;
+    a.chk = ctx->zp.ch64;
+    a.zs = ctx->d_zsum64;
+    a.rho = nullptr;
+    return a;
+}
+
+template <typename real>
+static void fill_args_t(const heat_ctx *ctx, void *dst)
+{
+    SweepArgs<real> a = make_args_t<real>(ctx);
+    a.Nr = ctx->g.Nr;
+    a.Nz = ctx->g.Nz;
+    a.G = a.band = 0;  // set by the plan
+    a.Rc = ctx->zp.Rc;
+    a.nch = ctx->zp.n_chunks;
+    a.rowcls = ctx->d_rowcls;
+    a.colcls = ctx->d_colcls;
+    a.R64 = ctx->dR.full;
+    a.Z64 = ctx->dZ.full;
+    for (int f = 0; f < 4; ++f) a.bc.th[f] = ctx->theta_bc[f];
+    a.ucls = ctx->zp.ucls;
+    a.zc = a.zs + (size_t)2 * a.nch * a.Nr;
+    a.f0 = static_cast<real *>(ctx->d_field[0]);
+    a.f1 = static_cast<real *>(ctx->d_field[1]);
+    *static_cast<SweepArgs<real> *>(dst) = a;
+}
+
+size_t args_bytes(int precision)
+{
+    return precision == HEAT_FP64 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>);
+}
+
+void fill_args(const heat_ctx *ctx, void *dst)
+{
+    if (ctx->precision == HEAT_FP64)
+        fill_args_t<double>(ctx, dst);
+    else
+        fill_args_t<float>(ctx, dst);
+}
+
+// Plan for n instances whose host arguments are in h (G and band are filled in).
+cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPlan &plan)
+{
+    switch (precision) {
+    case HEAT_FP64: return plan_fp64(static_cast<SweepArgs<double> *>(h), n, req, plan);
+    case HEAT_FP32: return plan_fp32(static_cast<SweepArgs<float> *>(h), n, req, plan);
+    default: return plan_fp32_refined(static_cast<SweepArgs<float> *>(h), n, req, plan);
     }
 }
 
-cudaError_t launch_sweep(heat_ctx *ctx, int dir)
+// Enqueue one half-step of a plan.  flip = 0 reads f0 and writes f1.
+cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s)
 {
-    return launch_sweep_buffers(ctx, dir, ctx->d_field[ctx->cur], ctx->d_field[1 - ctx->cur]);
-}
-
-cudaError_t launch_steps(heat_ctx *ctx, int n)
-{
-    for (int s = 0; s < n; ++s) {
-        cudaError_t e = launch_sweep_buffers(ctx, 0, ctx->d_field[ctx->cur], ctx->d_field[1 - ctx->cur]);
-        if (e != cudaSuccess) return e;
-        e = launch_sweep_buffers(ctx, 1, ctx->d_field[1 - ctx->cur], ctx->d_field[ctx->cur]);
+    for (const Launch &L : plan.dir[dir]) {
+        void *kargs[2] = {(void *)&d_args, (void *)&flip};
+        cudaError_t e = cudaLaunchKernel(L.fn, L.grid, L.block, kargs, L.smem, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// r-sweep: 1 launch; z-sweep: 3 (summaries, carries, solve), 6 on the refined path.
-int launches_per_step(const heat_ctx *ctx) { return ctx->precision == HEAT_FP32_REFINED ? 7 : 4; }
+// (Re)build the single-instance plan of a context and upload its arguments.
+cudaError_t ctx_plan(heat_ctx *ctx)
+{
+    ctx->h_args.assign(args_bytes(ctx->precision), 0);
+    fill_args(ctx, ctx->h_args.data());
+    cudaError_t e = make_plan(ctx->precision, ctx->h_args.data(), 1, Tuning(), ctx->plan);
+    if (e != cudaSuccess) return e;
+    if (!ctx->d_args && (e = cudaMalloc(&ctx->d_args, ctx->h_args.size())) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(ctx->d_args, ctx->h_args.data(), ctx->h_args.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(ctx->stream);
+}
+
+cudaError_t launch_sweep(heat_ctx *ctx, int dir)
+{
+    return run_plan(ctx->plan, dir, ctx->d_args, ctx->cur, ctx->stream);
+}
+
+cudaError_t launch_steps(heat_ctx *ctx, int n)
+{
+    for (int s = 0; s < n; ++s) {
+        cudaError_t e = run_plan(ctx->plan, 0, ctx->d_args, ctx->cur, ctx->stream);
+        if (e != cudaSuccess) return e;
+        e = run_plan(ctx->plan, 1, ctx->d_args, 1 - ctx->cur, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int launches_per_step(const heat_ctx *ctx) { return (int)(ctx->plan.dir[0].size() + ctx->plan.dir[1].size()); }
 
 int energy_blocks(const heat_ctx *ctx)
 {

@@ -3,9 +3,9 @@
 
 namespace heat {
 
-cudaError_t sweep_fp32(heat_ctx *ctx, int dir, const void *a, void *b)
+cudaError_t plan_fp32(SweepArgs<float> *h, int n, const Tuning &req, SweepPlan &plan)
 {
-    return sweep_mode<float, MODE_DELTA>(ctx, dir, (const float *)a, (float *)b, ctx->dR.t32, ctx->dZ.t32);
+    return plan_mode<float, MODE_DELTA>(h, n, req, plan);
 }
 
 }  // namespace heat

@@ -3,9 +3,9 @@
 
 namespace heat {
 
-cudaError_t sweep_fp64(heat_ctx *ctx, int dir, const void *a, void *b)
+cudaError_t plan_fp64(SweepArgs<double> *h, int n, const Tuning &req, SweepPlan &plan)
 {
-    return sweep_mode<double, MODE_LIT>(ctx, dir, (const double *)a, (double *)b, ctx->dR.t64, ctx->dZ.t64);
+    return plan_mode<double, MODE_LIT>(h, n, req, plan);
 }
 
 }  // namespace heat

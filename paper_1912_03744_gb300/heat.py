@@ -23,7 +23,9 @@ NUMPY_DTYPE = {"fp64": np.float64, "fp32": np.float32, "fp32_refined": np.float3
 # Every extern "C" symbol include/heat.h declares.
 SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field", "heat_set_field", "heat_energy",
            "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror",
-           "heat_energy_noalloc"]
+           "heat_energy_noalloc", "heat_batch_create", "heat_batch_member", "heat_batch_step", "heat_batch_sync",
+           "heat_batch_tune", "heat_batch_set_tuning", "heat_batch_get_tuning", "heat_batch_launches_per_step",
+           "heat_batch_destroy"]
 
 
 class HeatError(RuntimeError):
@@ -83,6 +85,17 @@ def load():
         L.heat_destroy.restype = None
         L.heat_strerror.argtypes = [ctypes.c_int]
         L.heat_strerror.restype = ctypes.c_char_p
+        L.heat_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(_Geometry), ctypes.POINTER(_Materials),
+                                         ctypes.POINTER(_Options), dp, vp, ctypes.POINTER(vp)]
+        L.heat_batch_member.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.heat_batch_step.argtypes = [vp, ctypes.c_int]
+        L.heat_batch_sync.argtypes = [vp]
+        L.heat_batch_tune.argtypes = [vp, ctypes.c_int, dp]
+        L.heat_batch_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.heat_batch_get_tuning.argtypes = [vp, ip, ip, ip]
+        L.heat_batch_launches_per_step.argtypes = [vp]
+        L.heat_batch_destroy.argtypes = [vp]
+        L.heat_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -95,6 +108,31 @@ def _check(fn, st):
 def _current_stream_handle():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _marshal(p, keep):
+    """heat_geometry and heat_materials of a problem; arrays they point to go in ``keep``."""
+    def arr(x, dt_):
+        a = np.ascontiguousarray(x, dtype=dt_)
+        keep.append(a)
+        return a
+
+    rf, rc = arr(p.r_faces, np.float64), arr(p.r_cells, np.int32)
+    zf, zc = arr(p.z_faces, np.float64), arr(p.z_cells, np.int32)
+    bx = np.asarray(p.boxes, dtype=np.float64).reshape(-1, 4)
+    boxes = (_Box * len(bx))(*[_Box(*map(float, b), int(r)) for b, r in zip(bx, p.box_region)])
+    keep.append(boxes)
+    geo = _Geometry(len(rc), rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    rc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                    len(zc), zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    zc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(bx), boxes,
+                    (ctypes.c_int * 4)(*[int(v) for v in p.bc]),
+                    (ctypes.c_double * 4)(*[float(v) for v in p.T_bc]))
+    k, C, q = arr(p.k, np.float64), arr(p.C, np.float64), arr(p.q, np.float64)
+    mat = _Materials(len(k), k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(p.T_init))
+    return geo, mat
 
 
 class HeatSolver:
@@ -113,27 +151,7 @@ class HeatSolver:
         L = load()
         p = problem
         self._keep = []
-
-        def arr(x, dt_):
-            a = np.ascontiguousarray(x, dtype=dt_)
-            self._keep.append(a)
-            return a
-
-        rf, rc = arr(p.r_faces, np.float64), arr(p.r_cells, np.int32)
-        zf, zc = arr(p.z_faces, np.float64), arr(p.z_cells, np.int32)
-        bx = np.asarray(p.boxes, dtype=np.float64).reshape(-1, 4)
-        boxes = (_Box * len(bx))(*[_Box(*map(float, b), int(r)) for b, r in zip(bx, p.box_region)])
-        self._keep.append(boxes)
-        geo = _Geometry(len(rc), rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                        rc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                        len(zc), zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                        zc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(bx), boxes,
-                        (ctypes.c_int * 4)(*[int(v) for v in p.bc]),
-                        (ctypes.c_double * 4)(*[float(v) for v in p.T_bc]))
-        k, C, q = arr(p.k, np.float64), arr(p.C, np.float64), arr(p.q, np.float64)
-        mat = _Materials(len(k), k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(p.T_init))
+        geo, mat = _marshal(p, self._keep)
         opt = _Options(PRECISION[precision], int(getattr(p, "face_mean", 0)))
         self.stream = stream
         sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _current_stream_handle()
@@ -219,3 +237,92 @@ class HeatSolver:
 
     def launches_per_step(self) -> int:
         return int(load().heat_launches_per_step(self._h))
+
+
+class _MemberView(HeatSolver):
+    """HeatSolver view of a batch member: the batch owns the context."""
+
+    def close(self):
+        pass
+
+
+class HeatBatch:
+    """A batched ensemble of independent ADI problems of one precision
+    (wraps heat_batch_*).  ``problems``: list of problem objects (each with
+    Nr <= 1024); ``dts``: one dt per member.  ``members[i]`` is a HeatSolver
+    view of member i for field / set_field / energy / centres; stepping is
+    done for all members at once by ``step``."""
+
+    def __init__(self, problems, dts, precision: str = "fp32", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("HeatBatch needs a CUDA GPU; there is no CPU path")
+        L = load()
+        n = len(problems)
+        self._keep = []
+        geos = (_Geometry * n)()
+        mats = (_Materials * n)()
+        for i, p in enumerate(problems):
+            geos[i], mats[i] = _marshal(p, self._keep)
+        fm = {int(getattr(p, "face_mean", 0)) for p in problems}
+        if len(fm) != 1:
+            raise ValueError("batch members must share the face mean")
+        opt = _Options(PRECISION[precision], fm.pop())
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        assert d.shape == (n,)
+        sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _current_stream_handle()
+        h = ctypes.c_void_p()
+        _check("heat_batch_create", L.heat_batch_create(n, geos, mats, ctypes.byref(opt),
+                                                        d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sh,
+                                                        ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.precision = precision
+        self.members = []
+        for i in range(n):
+            c = ctypes.c_void_p()
+            _check("heat_batch_member", L.heat_batch_member(h, i, ctypes.byref(c)))
+            m = _MemberView.__new__(_MemberView)
+            m._h, m._owner, m._keep, m.precision, m.stream = c, self, [], precision, stream
+            nr, nz, te = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+            _check("heat_info", L.heat_info(c, ctypes.byref(nr), ctypes.byref(nz), None, None, ctypes.byref(te)))
+            m.Nr, m.Nz, m.tau_exp, m.dt = nr.value, nz.value, te.value, float(d[i])
+            self.members.append(m)
+        self.cells = sum(m.Nr * m.Nz for m in self.members)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None  # member handles die with the batch
+            load().heat_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check("heat_batch_step", load().heat_batch_step(self._h, int(n)))
+
+    def sync(self):
+        _check("heat_batch_sync", load().heat_batch_sync(self._h))
+
+    def tune(self, trial_steps: int = 5) -> float:
+        """Autotune the schedule (fields are left unchanged); returns ms/step of the winner."""
+        ms = ctypes.c_double()
+        _check("heat_batch_tune", load().heat_batch_tune(self._h, int(trial_steps), ctypes.byref(ms)))
+        return ms.value
+
+    def set_tuning(self, rK: int = 0, band: int = 0, zwpb: int = 0):
+        _check("heat_batch_set_tuning", load().heat_batch_set_tuning(self._h, int(rK), int(band), int(zwpb)))
+
+    def tuning(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check("heat_batch_get_tuning", load().heat_batch_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                                     ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def launches_per_step(self) -> int:
+        return int(load().heat_batch_launches_per_step(self._h))

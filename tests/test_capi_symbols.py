@@ -49,3 +49,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.heat_create(None, None, None, 1.0, None, ctypes.byref(h)) == -1
     assert L.heat_step(None, 1) == -1
     assert L.heat_sweep(None, 0) == -1
+
+
+def test_batch_arguments_rejected_without_gpu():
+    from paper_1912_03744_gb300 import heat as hb
+    L = hb.load()
+    h = ctypes.c_void_p()
+    assert L.heat_batch_create(0, None, None, None, None, None, ctypes.byref(h)) == -1
+    assert L.heat_batch_create(1, None, None, None, None, None, None) == -1
+    assert L.heat_batch_step(None, 1) == -1
+    assert L.heat_batch_tune(None, 1, None) == -1
+    assert L.heat_batch_set_tuning(None, 8, 0, 0) == -1
+    assert L.heat_batch_member(None, 0, ctypes.byref(h)) == -1
+    assert L.heat_batch_launches_per_step(None) == -1
