@@ -11,7 +11,8 @@ Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
 with an event between the two sweeps for per-kernel durations.
 `value` = active cells x K / (sum of step times).  `e2e` runs the same job
 through the C ABI with host buffers: upload of the initial field, K steps,
-download of the result, timed as a whole.
+download of the result, timed as a whole.  `ensemble` times the 512-member
+batched ensemble (500 graph-replayed steps under the autotuned schedule).
 
 --impl reference times the FP64 CPU oracle (the method's plain restatement,
 OpenMP over lines as in the paper's Sec. 4) on a bounded number of steps of
@@ -174,12 +175,48 @@ def time_e2e(p, precision, steps):
     return t1 - t0, nbytes
 
 
-def active_cells(p):
-    from oracle import Oracle  # grid region map only, for counting
-    o = Oracle(p)
-    n = int((o.grid()["region"] >= 0).sum())
-    del o
-    return n
+def active_cells(solver, p):
+    """Cells whose centre (from the library's grid) lies in a region box."""
+    rc, zc = solver.centres()
+    act = np.zeros((len(zc), len(rc)), dtype=bool)
+    for (r0, r1, z0, z1) in np.asarray(p.boxes, dtype=np.float64).reshape(-1, 4):
+        act |= ((zc >= z0) & (zc <= z1))[:, None] & ((rc >= r0) & (rc <= r1))[None, :]
+    return int(act.sum())
+
+
+def time_ensemble(steps, warmup, precision="fp32"):
+    """The 512-member batched ensemble (Nr 64..512, Nz 128..1024, jittered
+    layers and materials), dt = 50 x each member's explicit limit, autotuned
+    schedule, graph-replayed steps; CUDA events on the caller's stream around
+    all timed steps.  The two field buffers (~0.7 GB in FP32) exceed L2."""
+    import torch
+    from paper_1912_03744_gb300 import HeatBatch
+    probs = H.config3_members(512)
+    t0 = time.perf_counter()
+    b = HeatBatch(probs, [1.0] * len(probs), precision=precision)
+    b.set_dt([H.DT_FACTOR * m.tau_exp for m in b.members])
+    create_s = time.perf_counter() - t0
+    act = sum(active_cells(m, p) for m, p in zip(b.members, probs))
+    tune_ms = b.tune(trial_steps=3)
+    b.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    b.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = all(np.isfinite(b.members[i].field()).all() for i in (0, len(probs) // 2, len(probs) - 1))
+    out = {"workload": "config3: 512-member ensemble, Nr U{64..512}, Nz U{128..1024}, seed 3, dt=50*tau_exp",
+           "precision": precision, "members": len(probs), "cells": b.cells, "active_cells": act,
+           "steps": steps, "ms_per_step": ms / steps, "cell_steps_per_s": act * steps / (ms * 1e-3),
+           "member_steps_per_s": len(probs) * steps / (ms * 1e-3),
+           "fields_per_s_500_steps": len(probs) / (500 * ms / steps * 1e-3),
+           "tuning": dict(zip(("rK", "band", "zwpb"), b.tuning())), "tune_ms_per_step": tune_ms,
+           "launches_per_step": b.launches_per_step(), "graph_replay": True, "create_s": create_s,
+           "finite": bool(ok), "l2": "inputs larger than L2"}
+    b.close()
+    return out
 
 
 def cpu_baseline(p, budget_s=12.0, max_steps=50):
@@ -204,7 +241,8 @@ def run_reference(args):
     if rank != 0:
         return
     p = H.config2()
-    act = active_cells(p)
+    from oracle import Oracle
+    act = int((Oracle(p).grid()["region"] >= 0).sum())
     n, dt, cores = cpu_baseline(p, budget_s=max(5.0, 0.5 * args.steps), max_steps=max(1, args.steps))
     v = act * n / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -227,6 +265,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-main", action="store_true",
                     help="time the headline path only (no side-by-side, e2e or CPU legs); for profiling")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=4096)
     args = ap.parse_args()
@@ -245,7 +285,10 @@ def main():
     __graft_entry__.build()
 
     p = H.config2(args.nr, args.nz)
-    act = active_cells(p)
+    from paper_1912_03744_gb300 import HeatSolver
+    probe = HeatSolver(p, 1.0, precision="fp64")
+    act = active_cells(probe, p)
+    probe.close()
     ncell = p.Nr * p.Nz
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     other = "fp64" if args.precision == "fp32" else "fp32"
@@ -262,6 +305,7 @@ def main():
     side_steps = max(3, min(args.steps, 200))
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
+    ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup)
     _barrier(ws)
 
     tot_ms = sum(main_t["r_ms"]) + sum(main_t["z_ms"])
@@ -306,6 +350,7 @@ def main():
                 "h2d_bytes_per_step": e2e_bytes / args.steps, "d2h_bytes_per_step": e2e_bytes / args.steps},
         "gpu_launches": main_t["launches"],
         "clocks": clk.summary(),
+        "ensemble": ens,
         "side_by_side": {other: {"value": act / (side_ms * 1e-3), "ms_per_step": side_ms,
                                  "steps": len(side_t["r_ms"]), "roofline": roof(side_t, other)}},
     }

@@ -209,6 +209,10 @@ int heat_batch_create(int n, const heat_geometry *geoms, const heat_materials *m
                       const heat_options *opt, const double *dts, void *stream,
                       heat_batch **out);
 
+/* Change every member's dt (dts[n], each > 0): rebuilds the members' tables
+ * and the batch's launch plan and graphs.  Synchronizes. */
+int heat_batch_set_dt(heat_batch *b, const double *dts);
+
 /* Borrow member i's context for heat_field, heat_set_field, heat_energy,
  * heat_info (and heat_step of that member alone).  The batch owns it:
  * heat_destroy on it does nothing, heat_sweep and heat_set_dt return

@@ -24,6 +24,7 @@ size_t args_bytes(int precision);
 void fill_args(const heat_ctx *ctx, void *dst);
 cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPlan &plan);
 cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s);
+int ctx_set_dt(heat_ctx *ctx, double dt);
 }  // namespace heat
 
 using namespace heat;
@@ -167,6 +168,22 @@ int heat_batch_create(int n, const heat_geometry *geoms, const heat_materials *m
     }
     *out = b;
     return HEAT_OK;
+}
+
+int heat_batch_set_dt(heat_batch *b, const double *dts)
+{
+    if (!b || !dts) return HEAT_ERR_ARG;
+    for (int i = 0; i < b->n; ++i)
+        if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return HEAT_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t ab = args_bytes(b->precision);
+    for (int i = 0; i < b->n; ++i) {
+        const int st = ctx_set_dt(b->m[i], dts[i]);
+        if (st != HEAT_OK) return st;
+        fill_args(b->m[i], b->h_args.data() + ab * i);  // table pointers may have moved
+    }
+    return cuda_status(apply_tuning(b, b->plan.used));
 }
 
 int heat_batch_member(heat_batch *b, int i, heat_ctx **ctx)

@@ -152,6 +152,23 @@ size_t elem_size(const heat_ctx *ctx) { return ctx->precision == HEAT_FP64 ? siz
 
 }  // namespace
 
+namespace heat {
+// heat_set_dt without the batch-member guard (the batch re-plans afterwards).
+int ctx_set_dt(heat_ctx *ctx, double dt)
+{
+    if (!ctx || !(dt > 0.0) || !std::isfinite(dt)) return HEAT_ERR_ARG;
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->tau = dt;
+    build_tables(ctx);
+    build_zpartition(ctx);
+    int st = upload_tab(ctx, ctx->R, ctx->dR);
+    if (st != HEAT_OK) return st;
+    if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
+    if ((st = upload_zpart(ctx)) != HEAT_OK) return st;
+    return cuda_status(ctx_plan(ctx));
+}
+}  // namespace heat
+
 extern "C" {
 
 const char *heat_strerror(int status)
@@ -238,18 +255,11 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     return HEAT_OK;
 }
 
+
 int heat_set_dt(heat_ctx *ctx, double dt)
 {
-    if (!ctx || !(dt > 0.0) || !std::isfinite(dt) || ctx->batch_member) return HEAT_ERR_ARG;
-    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
-    ctx->tau = dt;
-    build_tables(ctx);
-    build_zpartition(ctx);
-    int st = upload_tab(ctx, ctx->R, ctx->dR);
-    if (st != HEAT_OK) return st;
-    if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
-    if ((st = upload_zpart(ctx)) != HEAT_OK) return st;
-    return cuda_status(ctx_plan(ctx));
+    if (!ctx || ctx->batch_member) return HEAT_ERR_ARG;
+    return ctx_set_dt(ctx, dt);
 }
 
 int heat_sweep(heat_ctx *ctx, int dir)

@@ -25,7 +25,7 @@ SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field"
            "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror",
            "heat_energy_noalloc", "heat_batch_create", "heat_batch_member", "heat_batch_step", "heat_batch_sync",
            "heat_batch_tune", "heat_batch_set_tuning", "heat_batch_get_tuning", "heat_batch_launches_per_step",
-           "heat_batch_destroy"]
+           "heat_batch_destroy", "heat_batch_set_dt"]
 
 
 class HeatError(RuntimeError):
@@ -88,6 +88,7 @@ def load():
         L.heat_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(_Geometry), ctypes.POINTER(_Materials),
                                          ctypes.POINTER(_Options), dp, vp, ctypes.POINTER(vp)]
         L.heat_batch_member.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.heat_batch_set_dt.argtypes = [vp, dp]
         L.heat_batch_step.argtypes = [vp, ctypes.c_int]
         L.heat_batch_sync.argtypes = [vp]
         L.heat_batch_tune.argtypes = [vp, ctypes.c_int, dp]
@@ -302,6 +303,13 @@ class HeatBatch:
             self.close()
         except Exception:
             pass
+
+    def set_dt(self, dts):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        assert d.shape == (self.n,)
+        _check("heat_batch_set_dt", load().heat_batch_set_dt(self._h, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        for m, x in zip(self.members, d):
+            m.dt = float(x)
 
     def step(self, n: int = 1):
         _check("heat_batch_step", load().heat_batch_step(self._h, int(n)))

@@ -166,3 +166,19 @@ def test_member_rules():
                                  T_init=300.0, q=0.0)
     with pytest.raises(HeatError):
         HeatBatch([probs[0], big], [1.0, 1.0], precision="fp32")
+
+
+def test_batch_set_dt():
+    """Created with dt = 1 s, switched to 50 x each member's explicit limit."""
+    from paper_1912_03744_gb300 import HeatBatch
+    sel = _pick(ENSEMBLE, 2, seed=6)
+    probs = [ENSEMBLE[i] for i in sel]
+    ref, dts = _oracle_runs(probs, 9)
+    b = HeatBatch(probs, [1.0] * len(probs), precision="fp32")
+    for m, d in zip(b.members, dts):
+        assert abs(H.DT_FACTOR * m.tau_exp - d) <= 1e-12 * d
+    b.set_dt(dts)
+    b.step(9)
+    for m, To in zip(b.members, ref):
+        assert _rel(m.field(), To) <= 1e-5
+    b.close()
