@@ -40,6 +40,10 @@ METRIC = "cell-steps/s vs HBM roofline"
 UNIT = "cell-steps/s"
 WORKLOAD = "config2: five-region layered cell 2048x4096, seed 2, dt=50*tau_exp"
 ELEM = {"fp64": 8, "fp32": 4}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of this workload (profiles/adi_step_config2_2048x4096_fp32.md);
+# None where no capture matches the current kernel.
+TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.952512e6 + 2.080000e6}
 
 
 def _peaks():
@@ -184,7 +188,7 @@ def active_cells(solver, p):
     return int(act.sum())
 
 
-def time_ensemble(steps, warmup, precision="fp32"):
+def time_ensemble(steps, warmup, precision="fp32", tuning=None):
     """The 512-member batched ensemble (Nr 64..512, Nz 128..1024, jittered
     layers and materials), dt = 50 x each member's explicit limit, autotuned
     schedule, graph-replayed steps; CUDA events on the caller's stream around
@@ -197,7 +201,11 @@ def time_ensemble(steps, warmup, precision="fp32"):
     b.set_dt([H.DT_FACTOR * m.tau_exp for m in b.members])
     create_s = time.perf_counter() - t0
     act = sum(active_cells(m, p) for m, p in zip(b.members, probs))
-    tune_ms = b.tune(trial_steps=3)
+    if tuning is None:
+        tune_ms = b.tune(trial_steps=3)
+    else:
+        b.set_tuning(*tuning)
+        tune_ms = None
     b.step(warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -267,6 +275,9 @@ def main():
                     help="time the headline path only (no side-by-side, e2e or CPU legs); for profiling")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=500)
+    ap.add_argument("--ensemble-only", action="store_true", help="time the ensemble leg only; for profiling")
+    ap.add_argument("--ensemble-tuning", default=None,
+                    help="K,band,zwpb: fixed ensemble schedule instead of the autotuner")
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=4096)
     args = ap.parse_args()
@@ -284,6 +295,11 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
 
+    ens_tuning = tuple(int(x) for x in args.ensemble_tuning.split(",")) if args.ensemble_tuning else None
+    if args.ensemble_only:
+        print(json.dumps({"ensemble_only": True, **time_ensemble(args.ensemble_steps, args.warmup,
+                                                                 tuning=ens_tuning)}), flush=True)
+        return
     p = H.config2(args.nr, args.nz)
     from paper_1912_03744_gb300 import HeatSolver
     probe = HeatSolver(p, 1.0, precision="fp64")
@@ -305,7 +321,7 @@ def main():
     side_steps = max(3, min(args.steps, 200))
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
-    ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup)
+    ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning)
     _barrier(ws)
 
     tot_ms = sum(main_t["r_ms"]) + sum(main_t["z_ms"])
@@ -327,7 +343,8 @@ def main():
         bytes_launch = 2 * ELEM[precision] * ncell  # read + write of every cell per sweep
         ach = bytes_launch / (avg * 1e-3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": ach / peak, "traffic": TRAFFIC.get((name, precision, p.Nr, p.Nz)),
+                "algorithmic_bytes": bytes_launch, "peak_kind": peak_kind,
                 "rsweep_ms": r_avg, "zsweep_ms": z_avg}
 
     side_ms = (sum(side_t["r_ms"]) + sum(side_t["z_ms"])) / len(side_t["r_ms"])
