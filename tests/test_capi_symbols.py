@@ -34,6 +34,24 @@ def test_binding_symbol_list_matches_header():
     assert sorted(SYMBOLS) == _declared("heat.h")
 
 
+def test_surrogate_symbols_exported_and_bound(lib):
+    from paper_1912_03744_gb300.surrogate import SURR_SYMBOLS
+    names = _declared("surrogate.h")
+    assert sorted(SURR_SYMBOLS) == names and len(names) == 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_surrogate_arguments_rejected_without_gpu():
+    from paper_1912_03744_gb300 import surrogate as sg
+    L = sg._lib()
+    h = ctypes.c_void_p()
+    assert L.surr_create(None, None, None, 0, 1.0, 1, 1, None, ctypes.byref(h)) == -1
+    assert L.surr_forward(None, None, 1, None, 0) == -1
+    assert L.surr_adam(None, 1e-3, 0.9, 0.999, 1e-8) == -1
+    assert L.surr_n_params(None) == 0
+
+
 def test_strerror_without_gpu(lib):
     lib.heat_strerror.restype = ctypes.c_char_p
     assert lib.heat_strerror(0) == b"ok"

@@ -1,0 +1,133 @@
+"""The surrogate's CUDA path (BF16 tensor-core GEMMs, FP32 accumulation)
+against the FP64 FNO oracle, through the C ABI.
+
+Tolerances: the GPU keeps weights and activations in BF16 (unit roundoff
+2^-9 = 2e-3), with about ten roundings in sequence per layer (DFTs, mode
+mixing, pointwise GEMM, activation) over 3 layers and the head; the
+expected relative error of the output and of each gradient block is
+therefore ~1e-2, and the bars below are 3e-2 (output, L2 over the rise)
+and 6e-2 (gradient blocks, L2)."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.fno_oracle import FnoOracle, S_Q
+from workloads import fno as F
+from workloads import heat as H
+
+pytestmark = pytest.mark.gpu
+
+D = F.MEDIUM           # 64 x 32 grid, width 16, 6 x 6 modes, 3 layers
+STEPS = 20
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _problem(params):
+    return H.config5_problem(params, Nr=D.Nr, Nz=D.Nz)
+
+
+def _setup(max_batch=8):
+    from paper_1912_03744_gb300 import Surrogate
+    params = H.config5_params(8, seed=21)
+    p0 = _problem(params[0])
+    ref = H.config5_reference_problem(Nr=D.Nr, Nz=D.Nz)
+    dt = H.DT_FACTOR * Oracle(ref).tau_exp()
+    s = Surrogate(p0, D, heater=H.HEATER, dt=dt, steps=STEPS, max_batch=max_batch)
+    g = Oracle(p0).grid()
+    fo = FnoOracle(D, g["rc"], g["zc"], p0.r_faces[-1], p0.z_faces[-1], T_init=p0.T_init)
+    return s, fo, params, dt
+
+
+def _blocks(d):
+    out, o = {}, 0
+    for name, shape in d.sizes():
+        n = int(np.prod(shape))
+        out[name] = slice(o, o + n)
+        o += n
+    return out
+
+
+def test_forward_matches_the_oracle():
+    s, fo, params, _ = _setup()
+    flat = F.random_params(D, 31).astype(np.float32)
+    s.set_params(flat)
+    assert s.n_params == D.n_params()
+    Tg = s.forward(params[:4])
+    To = fo.forward(flat.astype(np.float64), params[:4])
+    rel = np.linalg.norm(Tg - To) / np.linalg.norm(To - 300.0)
+    assert rel <= 3e-2, rel
+    # more samples than max_batch: chunked forward gives the same fields
+    s2 = s.forward(np.concatenate([params, params[:3]]))
+    np.testing.assert_array_equal(s2[:4], Tg)
+    s.close()
+
+
+def test_gradient_matches_the_oracle_block_by_block():
+    s, fo, params, _ = _setup()
+    flat = F.random_params(D, 32).astype(np.float32)
+    s.set_params(flat)
+    rng = np.random.default_rng(33)
+    B = 4
+    Tt = 300.0 + S_Q * params[:B, 5, None, None] * rng.uniform(0.0, 1.0, (B, D.Nz, D.Nr))
+    lg, gg = s.loss_grad(params[:B], Tt.astype(np.float32))
+    lo, go = fo.grad(flat.astype(np.float64), params[:B], Tt.astype(np.float32).astype(np.float64))
+    assert abs(lg - lo) <= 2e-2 * lo
+    for name, sl in _blocks(D).items():
+        num = np.linalg.norm(gg[sl] - go[sl])
+        den = np.linalg.norm(go[sl])
+        assert num <= 6e-2 * den, (name, num / den)
+    s.close()
+
+
+def test_adam_first_step_closed_form():
+    s, _, params, _ = _setup()
+    flat = F.random_params(D, 34).astype(np.float32)
+    s.set_params(flat)
+    Tt = np.full((2, D.Nz, D.Nr), 300.0, dtype=np.float32)
+    _, g = s.loss_grad(params[:2], Tt)
+    s.adam(1e-3, eps=1e-30)
+    w1 = s.get_params()
+    np.testing.assert_allclose(w1, flat - 1e-3 * np.sign(g), rtol=0, atol=2e-6)
+    s.close()
+
+
+def test_solver_path_matches_the_oracle():
+    s, _, params, dt = _setup()
+    T = s.solve(params[:2])
+    for b in range(2):
+        o = Oracle(_problem(params[b]))
+        o.step(dt, STEPS)
+        To = o.field()
+        assert np.max(np.abs(T[b] - To)) / np.max(np.abs(To)) <= 1e-5
+    s.close()
+
+
+def test_training_on_solver_data_reduces_the_loss():
+    s, _, params, _ = _setup()
+    s.set_params(F.init_params(D, 35).astype(np.float32))
+    T = s.solve(params)
+    l0, _ = s.loss_grad(params, T, want_grad=False)
+    for _ in range(40):
+        s.loss_grad(params, T, want_grad=False)
+        s.adam(3e-3)
+    l1, _ = s.loss_grad(params, T, want_grad=False)
+    assert l1 < 0.3 * l0, (l0, l1)
+    s.close()
+
+
+def test_fallback_returns_the_solver_fields_when_the_check_fails():
+    s, _, params, _ = _setup()
+    s.set_params(F.random_params(D, 36).astype(np.float32))  # untrained: far off
+    T, used, err = s.infer_checked(params[:5], n_check=2, tol=0.01, seed=3)
+    assert used and err > 0.01
+    np.testing.assert_array_equal(T, s.solve(params[:5]))
+    s.close()
