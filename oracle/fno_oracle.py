@@ -21,11 +21,15 @@ Definition:
             kz in {0..mz-1, Nz-mz..Nz-1} and kr in {0..mr-1}, with a complex
             C x C matrix R per kept mode
   project   h = gelu(Q1 v_L + q1b),  u = Q2 h + q2b          (2 channels)
-  output    T = T_init + S_Q q u_0 + (T_D - T_init) u_1
+  output    T = T_init + m (S_Q q u_0 + (T_D - T_init) u_1)
   loss      mean over samples and cells of ((T - T_true) / (S_Q q))^2
 The output head is linear in q and T_D because the discrete heat equation
 is linear in its source and its Dirichlet value (Sec. 3, eqs.
 "scheme_eq_1", "scheme_eq_2"): T - T_init = q G(k) + (T_D - T_init) H(k).
+m is the active-cell indicator of the geometry (1 where the cell centre
+lies in a region box, 0 on void cells): the scheme keeps void cells at
+T_init (identity rows), so the field jumps at the void's edge, a jump the
+network is not asked to reproduce.
 gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).
 """
 from __future__ import annotations
@@ -52,10 +56,13 @@ class FnoOracle:
     """FNO forward, loss, backward and Adam in FP64.
 
     d: a ``workloads.fno.FnoDims``; rc [Nr], zc [Nz]: cell centres; R, Z: the
-    outer radius and height used to scale the coordinates."""
+    outer radius and height used to scale the coordinates; active [Nz, Nr]:
+    the active-cell indicator m (all ones if None)."""
 
-    def __init__(self, d, rc, zc, R, Z, T_init=300.0):
+    def __init__(self, d, rc, zc, R, Z, T_init=300.0, active=None):
         self.d = d
+        self.m = np.ones((d.Nz, d.Nr)) if active is None else np.asarray(active, dtype=np.float64)
+        assert self.m.shape == (d.Nz, d.Nr)
         self.rc = np.asarray(rc, dtype=np.float64)
         self.zc = np.asarray(zc, dtype=np.float64)
         assert self.rc.shape == (d.Nr,) and self.zc.shape == (d.Nz,)
@@ -138,7 +145,7 @@ class FnoOracle:
         h = gelu(hpre)
         u = np.einsum("oh,bhzr->bozr", w["Q2"], h) + w["q2b"][None, :, None, None]
         q, Td = p[:, 5], p[:, 6]
-        T = self.T_init + (S_Q * q)[:, None, None] * u[:, 0] + (Td - self.T_init)[:, None, None] * u[:, 1]
+        T = self.T_init + self.m[None] * ((S_Q * q)[:, None, None] * u[:, 0] + (Td - self.T_init)[:, None, None] * u[:, 1])
         cache.update(hpre=hpre, h=h, u=u, p=p)
         return (T, cache) if keep else T
 
@@ -159,7 +166,7 @@ class FnoOracle:
         e = (T - np.asarray(T_true, dtype=np.float64)) / sc
         Ntot = e.size
         L = float(np.mean(e * e))
-        gT = 2.0 * e / sc / Ntot
+        gT = 2.0 * e / sc / Ntot * self.m[None]
         gu = np.stack([gT * sc, gT * (Td - self.T_init)[:, None, None]], axis=1)
         g = {}
         g["Q2"] = np.einsum("bozr,bhzr->oh", gu, c["h"])
