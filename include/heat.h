@@ -225,17 +225,22 @@ int heat_batch_step(heat_batch *b, int n);
 /* Wait for the batch stream. */
 int heat_batch_sync(heat_batch *b);
 
-/* Autotuner: time every valid schedule (r-sweep cells per thread K, rows
- * per line slot, z-solve warps per block) for trial_steps (1..1000) steps
+/* Autotuner: time every valid schedule (r-sweep kernel and its cells per
+ * thread K, rows per line slot, z-solve warps per block) for trial_steps (1..1000) steps
  * each, on the members' current fields, and keep the fastest.  The members'
  * fields are saved before and restored after, so the state does not change.
  * Allocates one temporary copy of all fields.  best_ms (may be NULL):
  * the winner's device time per step. */
 int heat_batch_tune(heat_batch *b, int trial_steps, double *best_ms);
 
-/* Set or read the schedule: rK in {0 (default), 4, 8, 16, 32}, band >= 0
- * (0 = default), zwpb in {0 (default), 1, 2}.  An invalid combination for
- * these members returns HEAT_ERR_ARG and keeps the current schedule. */
+/* Set or read the schedule.  rK selects the r-sweep: 1 = line teams (a team
+ * of lanes walks each r-line, 8 cells per lane in FP32, 4 in FP64; FP64 and
+ * FP32 only, lines up to 4096 FP32 / 2048 FP64 cells); 4, 8, 16, 32 = one
+ * line per thread group with rK cells per thread; 0 = default (line teams
+ * where every member allows them).  band >= 0: rows per line slot (line
+ * teams: rows per team when sizing the grid), 0 = default.  zwpb in
+ * {0 (default), 1, 2}.  An invalid combination for these members returns
+ * HEAT_ERR_ARG and keeps the current schedule. */
 int heat_batch_set_tuning(heat_batch *b, int rK, int band, int zwpb);
 int heat_batch_get_tuning(heat_batch *b, int *rK, int *band, int *zwpb);
 

@@ -17,6 +17,8 @@ void build_grid(const heat_geometry *, Grid &);
 void build_tables(heat_ctx *);
 void compute_limits(heat_ctx *);
 void build_zpartition(heat_ctx *);
+bool build_rline(const heat_ctx *, int, size_t, int &, int &, std::vector<double> &, std::vector<double> &,
+                 std::vector<double> &, std::vector<double> &, std::vector<int> &);
 cudaError_t launch_fill(heat_ctx *, int, double);
 cudaError_t launch_steps(heat_ctx *, int);
 cudaError_t launch_sweep(heat_ctx *, int);
@@ -135,6 +137,57 @@ int upload_zpart(heat_ctx *ctx)
     return HEAT_OK;
 }
 
+template <typename real>
+int upload_rline_t(heat_ctx *ctx, const std::vector<double> *src[4], const std::vector<int> &zcl)
+{
+    // zcl is followed by the row units: runs of up to kRLineR rows of one class
+    size_t n = 0;
+    for (int a = 0; a < 4; ++a) n += src[a]->size();
+    std::vector<real> h(n);
+    size_t o = 0;
+    for (int a = 0; a < 4; ++a)
+        for (double v : *src[a]) h[o++] = (real)v;
+    if (ctx->d_rl) cudaFree(ctx->d_rl), ctx->d_rl = nullptr;
+    if (ctx->d_rlz) cudaFree(ctx->d_rlz), ctx->d_rlz = nullptr;
+    HEAT_CHECK(cudaMalloc(&ctx->d_rl, n * sizeof(real)));
+    HEAT_CHECK(cudaMalloc(&ctx->d_rlz, zcl.size() * sizeof(int)));
+    HEAT_CHECK(cudaMemcpyAsync(ctx->d_rl, h.data(), n * sizeof(real), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_CHECK(cudaMemcpyAsync(ctx->d_rlz, zcl.data(), zcl.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    return HEAT_OK;
+}
+
+// Build and upload the line-team r-sweep tables (literal and increment forms
+// only; the refined path and lines too long for a team buffer keep the
+// block-line r-sweep).
+int upload_rline(heat_ctx *ctx)
+{
+    ctx->rl_LW = ctx->rl_nseg = 0;
+    if (ctx->precision == HEAT_FP32_REFINED) return HEAT_OK;
+    const bool f64 = ctx->precision == HEAT_FP64;
+    std::vector<double> tA, tB, tD, tC;
+    std::vector<int> zcl;
+    int LW = 0, nseg = 0;
+    if (!build_rline(ctx, f64 ? rline_K<double>() : rline_K<float>(), kRLineMaxBuf, LW, nseg, tA, tB, tD, tC, zcl))
+        return HEAT_OK;
+    const int nchunk = (int)zcl.size();
+    const Grid &g = ctx->g;
+    for (int j = 0; j < g.Nz;) {
+        int n = 1;
+        while (n < kRLineR && j + n < g.Nz && g.rowcls[j + n] == g.rowcls[j]) ++n;
+        zcl.push_back(j | (n << 16));
+        j += n;
+    }
+    ctx->rl_nunits = (int)zcl.size() - nchunk;
+    ctx->rl_nchunk = nchunk;
+    const std::vector<double> *src[4] = {&tA, &tB, &tD, &tC};
+    const int st = f64 ? upload_rline_t<double>(ctx, src, zcl) : upload_rline_t<float>(ctx, src, zcl);
+    if (st != HEAT_OK) return st;
+    ctx->rl_LW = LW;
+    ctx->rl_nseg = nseg;
+    return HEAT_OK;
+}
+
 void free_ctx(heat_ctx *ctx)
 {
     if (!ctx) return;
@@ -142,7 +195,7 @@ void free_ctx(heat_ctx *ctx)
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
                     ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,
-                    ctx->d_args};
+                    ctx->d_args,   ctx->d_rl,       ctx->d_rlz};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -165,6 +218,7 @@ int ctx_set_dt(heat_ctx *ctx, double dt)
     if (st != HEAT_OK) return st;
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
     if ((st = upload_zpart(ctx)) != HEAT_OK) return st;
+    if ((st = upload_rline(ctx)) != HEAT_OK) return st;
     return cuda_status(ctx_plan(ctx));
 }
 }  // namespace heat
@@ -225,6 +279,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     if ((st = upload_tab(ctx, ctx->R, ctx->dR)) != HEAT_OK) return fail(st);
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return fail(st);
     if ((st = upload_zpart(ctx)) != HEAT_OK) return fail(st);
+    if ((st = upload_rline(ctx)) != HEAT_OK) return fail(st);
     std::vector<double> wr(g.Nr), wz(g.Nz);
     for (int i = 0; i < g.Nr; ++i) wr[i] = 2.0 * kPi * g.rc[i] * g.hbar[i];
     for (int j = 0; j < g.Nz; ++j) wz[j] = g.etabar[j];

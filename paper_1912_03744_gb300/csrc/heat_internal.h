@@ -56,6 +56,35 @@ struct LineTab64 {
     const double *cap, *dsum, *dbc;
 };
 
+// Tables of the line-team r-sweep (heat_rline.cuh) for chunks of K cells,
+// teams of LW lanes and nseg segments of LW*K cells per line (Npad = nseg LW K
+// cells, the padding cells having all-zero entries).  Per row class:
+//   tA [Npad][4]  increment form {xm, xp, q, inv}, literal form {w, s, 0, inv}
+//   tB [Npad][2]  {f, wB}: wB_k = inv_k prod_{m=k+1}^{e} f_m (e = chunk end)
+//   tD [Npad][2]  {cp, wC}: wC_k = prod_{m=c0}^{k-1} cp_m (c0 = chunk start)
+//   tC [Npad/K][12] per chunk c (lane t = c mod LW of its segment):
+//        m_l = prod of F over chunks c-2^l+1..c (0 if t < 2^l), l = 0..4,
+//        Fe  = prod of F over the segment's chunks before c,
+//        n_l = prod of H over chunks c..c+2^l-1 (0 if t + 2^l >= LW),
+//        He  = prod of H over the segment's chunks after c,
+//      with F, H the products of f, cp over a chunk.
+// zcl [Npad/K]: column class shared by every cell of chunk c, or -1.
+// Cells per lane chunk of the line-team r-sweep: 8 (FP32), 4 (FP64).
+template <typename real>
+constexpr int rline_K() { return sizeof(real) == 4 ? 8 : 4; }
+// Largest per-team shared-memory buffer (one line's forward results).
+constexpr size_t kRLineMaxBuf = 16 * 1024;
+
+template <typename real>
+struct RLine {
+    const real *tA, *tB, *tD, *tC;
+    const int *zcl, *unit;  // unit [n_units]: j0 | (rows << 16), runs of up to kRLineR
+                            // consecutive rows of one row class, in order
+    int LW, nseg, n_units;
+};
+// Rows a line team solves together (one unit).
+constexpr int kRLineR = 2;
+
 // theta_bc of the faces r_lo, r_hi, z_lo, z_hi
 struct BcVals {
     double th[4];
@@ -74,6 +103,7 @@ struct SweepArgs {
     const int *rowcls, *colcls;
     LineTab<real> R, Z;
     LineTab64 R64, Z64;
+    RLine<real> rl;           // line-team r-sweep tables (tA == nullptr: not built)
     BcVals bc;
     const real *pkA, *pkB, *chk;
     const int *ucls;
@@ -93,7 +123,8 @@ struct Launch {
 // Launch schedule of both half-steps for one set of instances (one problem,
 // or a batch sharing precision), with the tunables it was built from.
 struct Tuning {
-    int rK = 0;    // r-sweep cells per thread (4, 8, 16, 32); 0 = default rule
+    int rK = 0;    // r-sweep: 1 = line-team kernel; 4, 8, 16, 32 = block-line kernel with rK
+                   // cells per thread; 0 = default rule (line teams where every instance has tables)
     int band = 0;  // r-sweep consecutive rows per line slot; 0 = default rule
     int zwpb = 0;  // z-solve warps per block (1 or 2); 0 = default rule
 };
@@ -185,6 +216,10 @@ struct heat_ctx {
     float *d_zsum = nullptr;       // z-sweep chunk summaries then carries (scratch), FP32 paths
     double *d_zsum64 = nullptr;    // z-sweep chunk summaries then carries (scratch), FP64 path
     float *d_rho = nullptr;        // refined path: FP32 residual field (scratch)
+    // line-team r-sweep tables (see RLine), in the field precision
+    void *d_rl = nullptr;
+    int *d_rlz = nullptr;
+    int rl_LW = 0, rl_nseg = 0, rl_nunits = 0, rl_nchunk = 0;
     // device
     heat::DevTab dR, dZ;
     int *d_rowcls = nullptr, *d_colcls = nullptr;

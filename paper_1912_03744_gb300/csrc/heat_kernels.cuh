@@ -55,6 +55,13 @@ enum { MODE_LIT = 0, MODE_DELTA = 1, MODE_REFINE = 2, MODE_CORR = 3 };
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+}  // namespace heat
+
+#include "heat_rline.cuh"
+#include "heat_zline.cuh"
+
+namespace heat {
+
 // Exclusive left-to-right scan of affine maps y = B + F x over segments of W
 // lanes.  On return (F, B) is the inclusive map, (Fe, Be) the exclusive one.
 template <typename real>
@@ -1281,6 +1288,73 @@ static cudaError_t plan_rsweep_k(SweepArgs<real> *h, int n, int band_req, Launch
     return cudaSuccess;
 }
 
+// Line-team r-sweep for n instances that all have their tables (rl.tA set).
+// One instance: a persistent grid (every resident block slot, lines dealt in
+// contiguous runs).  A batch: blockIdx.y = member, and enough blocks along x
+// that the member with the most line teams' worth of rows gets `band` rows per
+// team (default: the largest band that still fills two waves).
+template <typename real, int MODE>
+static cudaError_t plan_rline(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
+{
+    constexpr int K = rline_K<real>();
+    constexpr int R = kRLineR;
+    const void *fn = (const void *)rline_kernel<real, K, R, MODE>;
+    int maxseg = 1;
+    for (int m = 0; m < n; ++m) {
+        if (!h[m].rl.tA) return cudaErrorInvalidValue;
+        maxseg = h[m].rl.nseg > maxseg ? h[m].rl.nseg : maxseg;
+    }
+    const size_t warp_buf = (size_t)32 * maxseg * K * R * sizeof(real);  // (32/LW) teams x R x Npad
+    int NW = (int)((64 * 1024) / warp_buf);
+    NW = NW < 1 ? 1 : (NW > 4 ? 4 : NW);
+    const size_t smem = (size_t)NW * warp_buf;
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * NW, smem)) != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    auto teams_per_block = [&](int m) { return NW * (32 / h[m].rl.LW); };
+    int gx = 1;
+    if (n == 1) {
+        const int U = h[0].rl.n_units;
+        const int need = (U + teams_per_block(0) - 1) / teams_per_block(0);
+        gx = kSMs * per_sm < need ? kSMs * per_sm : need;
+        tu.band = (U + gx * teams_per_block(0) - 1) / (gx * teams_per_block(0));
+    } else {
+        auto blocks_for = [&](int band, long long *tot) {
+            int mx = 1;
+            *tot = 0;
+            for (int m = 0; m < n; ++m) {
+                const int U = h[m].rl.n_units;
+                const int bx = (U + teams_per_block(m) * band - 1) / (teams_per_block(m) * band);
+                *tot += bx;
+                mx = bx > mx ? bx : mx;
+            }
+            return mx;
+        };
+        int band = tu.band;
+        if (band <= 0) {
+            band = 1;
+            for (int b = 16; b > 1; b >>= 1) {
+                long long tot;
+                blocks_for(b, &tot);
+                if (tot >= 2LL * kSMs * per_sm) { band = b; break; }
+            }
+        }
+        long long tot;
+        gx = blocks_for(band, &tot);
+        tu.band = band;
+    }
+    for (int m = 0; m < n; ++m) h[m].band = tu.band, h[m].G = 32;
+    tu.rK = 1;
+    L.fn = fn;
+    L.grid = dim3(gx, n, 1);
+    L.block = dim3(32 * NW, 1, 1);
+    L.smem = smem;
+    L.flip = true;
+    return cudaSuccess;
+}
+
 template <typename real, int MODE>
 static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
@@ -1320,27 +1394,30 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
         maxNch = h[m].nch > maxNch ? h[m].nch : maxNch;
     }
     const int groups = (maxNr + COLS - 1) / COLS;
+    constexpr bool lean = MODE == MODE_LIT || MODE == MODE_DELTA;  // heat_zline.cuh passes
     Launch a, b, c;
     constexpr int SWPB = 4;
-    a.fn = (const void *)zsum_kernel<real, V, MODE>;
+    a.fn = lean ? (const void *)zsum2_kernel<real, V, lean ? MODE : MODE_DELTA> : (const void *)zsum_kernel<real, V, MODE>;
     a.grid = dim3((groups + SWPB - 1) / SWPB, maxNch, n);
     a.block = dim3(32 * SWPB, 1, 1);
-    a.smem = (size_t)SWPB * maxRc * 8 * sizeof(real);
+    a.smem = lean ? 0 : (size_t)SWPB * maxRc * 8 * sizeof(real);
     a.flip = true;
     cudaError_t e = allow_smem(a.fn, a.smem);
     if (e != cudaSuccess) return e;
-    b.fn = (const void *)zcarry_kernel<real>;
+    if (maxNch > ZSEG2 * ZMAXM) return cudaErrorInvalidValue;
+    b.fn = (const void *)zcarry2_kernel<real>;
     b.grid = dim3((maxNr + 31) / 32, n, 1);
-    b.block = dim3(32 * ZSEG, 1, 1);
+    b.block = dim3(32 * ZSEG2, 1, 1);
     b.smem = 0;
     b.flip = false;
     int wpb = tu.zwpb;
     if (wpb != 1 && wpb != 2) wpb = (size_t)maxRc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
     tu.zwpb = wpb;
-    c.fn = (const void *)zsolve_kernel<real, V, MODE>;
+    c.fn = lean ? (const void *)zsolve2_kernel<real, V, lean ? MODE : MODE_DELTA>
+                : (const void *)zsolve_kernel<real, V, MODE>;
     c.grid = dim3((groups + wpb - 1) / wpb, maxNch, n);
     c.block = dim3(32 * wpb, 1, 1);
-    c.smem = (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
+    c.smem = lean ? (size_t)wpb * maxRc * COLS * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
     c.flip = true;
     if ((e = allow_smem(c.fn, c.smem)) != cudaSuccess) return e;
     out.push_back(a);
@@ -1356,7 +1433,18 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     plan = SweepPlan();
     Tuning tu = req;
     Launch r;
-    cudaError_t e = plan_rsweep<real, MODE>(h, n, tu, r);
+    cudaError_t e = cudaErrorInvalidValue;
+    bool line_tables = MODE == MODE_LIT || MODE == MODE_DELTA;
+    for (int m = 0; m < n && line_tables; ++m) line_tables = h[m].rl.tA != nullptr;
+    if constexpr (MODE == MODE_LIT || MODE == MODE_DELTA) {
+        // rK: 0 = line teams where possible, 1 = line teams, 4..32 = block lines
+        if (tu.rK == 1 && !line_tables) return cudaErrorInvalidValue;
+        if (tu.rK <= 1 && line_tables) e = plan_rline<real, MODE>(h, n, tu, r);
+    }
+    if (e == cudaErrorInvalidValue) {
+        if (tu.rK == 1) tu.rK = 0;
+        e = plan_rsweep<real, MODE>(h, n, tu, r);
+    }
     if (e != cudaSuccess) return e;
     plan.dir[0].push_back(r);
     if constexpr (MODE == MODE_REFINE) {

@@ -345,3 +345,105 @@ void compute_limits(heat_ctx *ctx)
 }
 
 }  // namespace heat
+
+namespace heat {
+
+// Tables of the line-team r-sweep (see RLine in heat_internal.h) for chunks of
+// K cells, from the FP64 factorization of every row class.  Returns false when
+// a team's shared-memory buffer (Npad reals) would exceed max_buf_bytes, in
+// which case the block-line r-sweep is used instead.
+bool build_rline(const heat_ctx *ctx, int K, size_t max_buf_bytes, int &LW, int &nseg, std::vector<double> &tA,
+                 std::vector<double> &tB, std::vector<double> &tD, std::vector<double> &tC, std::vector<int> &zcl)
+{
+    const HostTab &R = ctx->R;
+    const int Nr = R.N, ncls = R.n_class;
+    const bool lit = ctx->precision == HEAT_FP64;
+    const size_t word = lit ? sizeof(double) : sizeof(float);
+    const int nch_line = (Nr + K - 1) / K;
+    LW = 4;
+    while (LW < 32 && LW < nch_line) LW <<= 1;
+    nseg = (nch_line + LW - 1) / LW;
+    const int nchunk = nseg * LW, Npad = nchunk * K;
+    if ((size_t)Npad * word > max_buf_bytes) return false;
+    tA.assign((size_t)ncls * Npad * 4, 0.0);
+    tB.assign((size_t)ncls * Npad * 2, 0.0);
+    tD.assign((size_t)ncls * Npad * 2, 0.0);
+    tC.assign((size_t)ncls * nchunk * 12, 0.0);
+    std::vector<double> F(nchunk), H(nchunk);
+    for (int a = 0; a < ncls; ++a) {
+        const size_t o = (size_t)a * Nr;
+        double *A = &tA[(size_t)a * Npad * 4], *B = &tB[(size_t)a * Npad * 2], *D = &tD[(size_t)a * Npad * 2];
+        for (int c = 0; c < nchunk; ++c) {
+            double inv[64], f[64], cp[64];
+            for (int k = 0; k < K; ++k) {
+                const int i = c * K + k;
+                const bool in = i < Nr;
+                inv[k] = in ? R.inv[o + i] : 0.0;
+                f[k] = in ? R.f[o + i] : 0.0;
+                cp[k] = in ? R.cp[o + i] : 0.0;
+                if (in) {
+                    double *e = &A[(size_t)i * 4];
+                    e[0] = lit ? R.w[o + i] : R.xm[o + i];
+                    e[1] = lit ? R.s[o + i] : R.xp[o + i];
+                    e[2] = lit ? 0.0 : R.q[o + i];
+                    e[3] = inv[k];
+                }
+            }
+            double tail = 1.0;
+            for (int k = K - 1; k >= 0; --k) {
+                const int i = c * K + k;
+                B[(size_t)i * 2] = f[k];
+                B[(size_t)i * 2 + 1] = inv[k] * tail;
+                tail *= f[k];
+            }
+            double head = 1.0;
+            for (int k = 0; k < K; ++k) {
+                const int i = c * K + k;
+                D[(size_t)i * 2] = cp[k];
+                D[(size_t)i * 2 + 1] = head;
+                head *= cp[k];
+            }
+            F[c] = tail;
+            H[c] = head;
+        }
+        double *C = &tC[(size_t)a * nchunk * 12];
+        for (int c = 0; c < nchunk; ++c) {
+            const int t = c % LW, c0 = c - t;
+            double *e = &C[(size_t)c * 12];
+            for (int l = 0; l < 5; ++l) {
+                const int span = 1 << l;
+                double m = 0.0, n = 0.0;
+                if (t >= span) {
+                    m = 1.0;
+                    for (int u = c - span + 1; u <= c; ++u) m *= F[u];
+                }
+                if (t + span < LW) {
+                    n = 1.0;
+                    for (int u = c; u < c + span; ++u) n *= H[u];
+                }
+                e[l] = m;
+                e[6 + l] = n;
+            }
+            double fe = 1.0, he = 1.0;
+            for (int u = c0; u < c; ++u) fe *= F[u];
+            for (int u = c + 1; u < c0 + LW; ++u) he *= H[u];
+            e[5] = fe;
+            e[11] = he;
+        }
+    }
+    zcl.assign(nchunk, 0);
+    const Grid &g = ctx->g;
+    for (int c = 0; c < nchunk; ++c) {
+        int cls = -2;
+        for (int k = 0; k < K; ++k) {
+            const int i = c * K + k;
+            if (i >= Nr) break;
+            if (cls == -2) cls = g.colcls[i];
+            else if (g.colcls[i] != cls) cls = -1;
+        }
+        zcl[c] = cls == -2 ? 0 : cls;
+    }
+    return true;
+}
+
+}  // namespace heat

@@ -55,6 +55,22 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
     for (int f = 0; f < 4; ++f) a.bc.th[f] = ctx->theta_bc[f];
     a.ucls = ctx->zp.ucls;
     a.zc = a.zs + (size_t)2 * a.nch * a.Nr;
+    a.rl = RLine<real>{};
+    if (ctx->rl_LW > 0) {
+        const int K = rline_K<real>();
+        const int nchunk = ctx->rl_nseg * ctx->rl_LW;
+        const size_t Npad = (size_t)nchunk * K, ncls = (size_t)ctx->R.n_class;
+        const real *base = static_cast<const real *>(ctx->d_rl);
+        a.rl.tA = base;
+        a.rl.tB = a.rl.tA + ncls * Npad * 4;
+        a.rl.tD = a.rl.tB + ncls * Npad * 2;
+        a.rl.tC = a.rl.tD + ncls * Npad * 2;
+        a.rl.zcl = ctx->d_rlz;
+        a.rl.unit = ctx->d_rlz + ctx->rl_nchunk;
+        a.rl.LW = ctx->rl_LW;
+        a.rl.nseg = ctx->rl_nseg;
+        a.rl.n_units = ctx->rl_nunits;
+    }
     a.f0 = static_cast<real *>(ctx->d_field[0]);
     a.f1 = static_cast<real *>(ctx->d_field[1]);
     *static_cast<SweepArgs<real> *>(dst) = a;

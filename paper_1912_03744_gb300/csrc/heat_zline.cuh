@@ -1,0 +1,467 @@
+// heat_zline.cuh -- the z-sweep (half-step 2 of the Peaceman-Rachford step,
+// Sec. 3, eq. "scheme_eq_2"; the line matrix is the axial operator of
+// eq. "Lambda_z" plus the mass term) in the literal and increment forms.
+//
+// Columns are strided, so lanes own columns: a warp owns 32 V adjacent
+// columns (V per lane, one 16-byte segment of a row, so each row access of
+// the warp is one contiguous run) and one chunk of Rc rows, and every lane
+// walks its chunk row by row (interleaved Thomas).  The column partition and
+// its carry algebra are those of ZPart (heat_internal.h):
+//   zsum   : each (column, chunk) to its two carry summaries B = sum r wB and
+//            G0 = sum r wG (r = right-hand side of the row);
+//   zcarry : the carry recurrences of every column over its chunks;
+//   zsolve : each chunk walked forward from its carry-in (results kept in
+//            shared memory) and back from its other carry, new field stored.
+// Rows are fetched ZP at a time and double-buffered: the loads of the next
+// ZP rows (and of the warp's left / right halo columns) are in flight while
+// the current ZP rows are computed.  Table rows of the lane's column class
+// are read through the read-only cache; a lane whose V columns straddle two
+// classes (a layer interface) reads them per column.
+#pragma once
+
+#include "heat_internal.h"
+
+namespace heat {
+
+constexpr int ZQ = 4;  // rows per fetch group
+
+template <typename real, int V>
+struct ZVec;
+template <>
+struct ZVec<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float (&v)[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct ZVec<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double (&v)[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x, v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&v)[2])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+};
+
+// The 8 packed table values {inv, f, cp, e0, e1, e2, wB, wG} of (class, row).
+template <typename real>
+__device__ __forceinline__ void zl_tab(const real *__restrict__ pkA, const real *__restrict__ pkB, size_t o,
+                                       real (&e)[8])
+{
+    if constexpr (sizeof(real) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(pkA + 4 * o));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(pkB + 4 * o));
+        e[0] = a.x, e[1] = a.y, e[2] = a.z, e[3] = a.w, e[4] = b.x, e[5] = b.y, e[6] = b.z, e[7] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(pkA + 4 * o + u));
+            const double2 b = __ldg(reinterpret_cast<const double2 *>(pkB + 4 * o + u));
+            e[u] = a.x, e[u + 1] = a.y, e[4 + u] = b.x, e[5 + u] = b.y;
+        }
+    }
+}
+
+// Per-lane state of a z walk over rows [j0, j1) of the lane's V columns.
+template <typename real, int V, int MODE>
+struct ZWalk {
+    static constexpr bool LIT = MODE == MODE_LIT;
+    const real *__restrict__ th;
+    const real *__restrict__ pkA;
+    const real *__restrict__ pkB;
+    const int *__restrict__ rowcls;
+    int Nr, Nz, ib, lane, j0, j1;
+    bool any, vec, uni, hasl, hasr, lo_edge, hi_edge;
+    int b[V];
+    int acur;
+    real ra[V], rb[V], rc[V], rd[V];  // increment: xm, xp of the row class; literal: am, ap, ad, sd
+    real bz_lo, bz_hi, br_lo, br_hi;  // ghost values beyond the outer faces
+    real tm[V], t[V];                 // rows j-1 and j of the walk
+
+    __device__ __forceinline__ void init(const SweepArgs<real> &A, const real *th_, int ib_, int lane_, int j0_,
+                                         int j1_)
+    {
+        th = th_, pkA = A.pkA, pkB = A.pkB, rowcls = A.rowcls;
+        Nr = A.Nr, Nz = A.Nz, ib = ib_, lane = lane_, j0 = j0_, j1 = j1_;
+        any = ib < Nr;
+        vec = (Nr % V) == 0;
+        lo_edge = ib == 0;
+        hi_edge = ib < Nr && ib + V >= Nr;
+        hasl = lane == 0 && ib > 0 && ib - 1 < Nr;
+        hasr = lane == 31 && ib + V < Nr;
+#pragma unroll
+        for (int q = 0; q < V; ++q) b[q] = ib + q < Nr ? A.colcls[ib + q] : (any ? A.colcls[ib] : 0);
+        uni = true;
+#pragma unroll
+        for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
+        acur = -1;
+        bz_lo = LIT ? real(0) : (real)A.bc.th[2];
+        bz_hi = LIT ? real(0) : (real)A.bc.th[3];
+        br_lo = LIT ? real(0) : (real)A.bc.th[0];
+        br_hi = LIT ? real(0) : (real)A.bc.th[1];
+    }
+    __device__ __forceinline__ void row_class(int a, const LineTab<real> &R)
+    {
+        if (a == acur) return;
+        acur = a;
+        const size_t ro = (size_t)a * Nr;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int i = ib + q;
+            const bool in = i < Nr;
+            if constexpr (LIT) {
+                ra[q] = in ? R.am[ro + i] : real(0);
+                rb[q] = in ? R.ap[ro + i] : real(0);
+                rc[q] = in ? R.ad[ro + i] : real(0);
+                rd[q] = in ? R.sd[ro + i] : real(0);
+            } else {
+                ra[q] = in ? R.xm[ro + i] : real(0);
+                rb[q] = in ? R.xp[ro + i] : real(0);
+            }
+        }
+    }
+    // row x of the lane's columns from src; ghost rows and columns hold theta_bc
+    __device__ __forceinline__ void row(const real *__restrict__ src, int x, real (&v)[V]) const
+    {
+        if (x < 0 || x >= Nz) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = x < 0 ? bz_lo : bz_hi;
+            return;
+        }
+        const real *p = src + (size_t)x * Nr + ib;
+        if (vec && any) {
+            ZVec<real, V>::ld(p, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : br_hi;
+        }
+    }
+    // fetch group: rows x+1 .. x+ZQ (the row after each of rows x .. x+ZQ-1)
+    // and the halo columns of rows x .. x+ZQ-1
+    struct Group {
+        real nx[ZQ][V];
+        real hl[ZQ], hr[ZQ];
+    };
+    __device__ __forceinline__ void fetch(int x, Group &G) const
+    {
+#pragma unroll
+        for (int p = 0; p < ZQ; ++p) {
+            const int jr = x + p;
+            if (jr < j1) {
+                row(th, jr + 1, G.nx[p]);
+                G.hl[p] = hasl ? th[(size_t)jr * Nr + ib - 1] : real(0);
+                G.hr[p] = hasr ? th[(size_t)jr * Nr + ib + V] : real(0);
+            }
+        }
+    }
+    // table values of row j for each column
+    __device__ __forceinline__ void tab(int j, real (&e)[V][8]) const
+    {
+        if (uni) {
+            real s8[8];
+            zl_tab(pkA, pkB, (size_t)b[0] * Nz + j, s8);
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) e[q][u] = s8[u];
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) zl_tab(pkA, pkB, (size_t)b[q] * Nz + j, e[q]);
+        }
+    }
+    // right-hand side of row j (then advance the row window): e[q] = table row of column q
+    __device__ __forceinline__ void rhs(int j, const Group &G, int p, const real (&e)[V][8], real (&d)[V])
+    {
+        real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
+        real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
+        if (hasl) tl = G.hl[p];
+        if (hasr) tr = G.hr[p];
+        if (lo_edge) tl = br_lo;
+        if (hi_edge) tr = br_hi;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const real x = t[q];
+            const real l = q > 0 ? t[q - 1] : tl;
+            const real r = q < V - 1 ? t[q + 1] : tr;
+            if constexpr (LIT) {
+                // e0 = s, e1 = w: (w + ad_r) x + am_r x_{i-1} + ap_r x_{i+1} + s + sd_r
+                d[q] = fmad(e[q][4] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, e[q][3] + rd[q])));
+            } else {
+                // e0 = q, e1 = xm_z, e2 = xp_z
+                real v = fmad(e[q][4], tm[q] - x, e[q][3]);
+                v = fmad(e[q][5], G.nx[p][q] - x, v);
+                v = fmad(ra[q], l - x, v);
+                d[q] = fmad(rb[q], r - x, v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = G.nx[p][q];
+    }
+    // Walk rows [j0, j1) calling emit(j, d, e) with the right-hand side d of
+    // row j and its table values e.
+    template <typename Emit>
+    __device__ __forceinline__ void walk(int ucls, const LineTab<real> &R, Emit emit)
+    {
+        row(th, j0 - 1, tm);
+        row(th, j0, t);
+        if (ucls >= 0) row_class(ucls, R);
+        Group A, B;
+        auto proc = [&](int x, const Group &G) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                const int j = x + p;
+                if (j < j1) {
+                    if (ucls < 0) row_class(rowcls[j], R);
+                    real e[V][8], d[V];
+                    tab(j, e);
+                    rhs(j, G, p, e, d);
+                    emit(j, d, e);
+                }
+            }
+        };
+        fetch(j0, A);
+#pragma unroll 1
+        for (int x = j0; x < j1; x += 2 * ZQ) {
+            const bool h1 = x + ZQ < j1;
+            if (h1) fetch(x + ZQ, B);
+            proc(x, A);
+            if (h1) {
+                if (x + 2 * ZQ < j1) fetch(x + 2 * ZQ, A);
+                proc(x + ZQ, B);
+            }
+        }
+    }
+};
+
+// Pass 1: summaries B = sum r wB and G0 = sum r wG of every (column, chunk):
+// zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks, instances).
+template <typename real, int V, int MODE>
+__global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
+{
+    const SweepArgs<real> &A = args[blockIdx.z];
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
+    if ((int)blockIdx.y >= A.nch) return;
+    const int lane = threadIdx.x & 31;
+    const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
+    const int c = blockIdx.y;
+    const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    ZWalk<real, V, MODE> W;
+    W.init(A, flip ? A.f1 : A.f0, grp * 32 * V + lane * V, lane, j0, j1);
+    real sb[V], sg[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) sb[q] = sg[q] = real(0);
+    W.walk(A.ucls[c], A.R, [&](int, const real(&d)[V], const real(&e)[V][8]) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            sb[q] = fmad(d[q], e[q][6], sb[q]);
+            sg[q] = fmad(d[q], e[q][7], sg[q]);
+        }
+    });
+    real *__restrict__ zs = A.zs;
+    if (W.vec) {
+        if (W.any) {
+            ZVec<real, V>::st(zs + ((size_t)c * 2) * Nr + W.ib, sb);
+            ZVec<real, V>::st(zs + ((size_t)c * 2 + 1) * Nr + W.ib, sg);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+            if (W.ib + q < Nr) {
+                zs[((size_t)c * 2) * Nr + W.ib + q] = sb[q];
+                zs[((size_t)c * 2 + 1) * Nr + W.ib + q] = sg[q];
+            }
+    }
+}
+
+// Pass 3: solve every (column, chunk) from its carries.  Shared memory holds
+// each warp's forward results, [warps][Rc][32 V] reals.
+template <typename real, int V, int MODE>
+__global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
+{
+    const SweepArgs<real> &A = args[blockIdx.z];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    real *__restrict__ out = flip ? A.f0 : A.f1;
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
+    if ((int)blockIdx.y >= A.nch) return;
+    constexpr int COLS = 32 * V;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = blockIdx.x * (blockDim.x >> 5) + w;
+    if (grp * COLS >= Nr) return;  // whole warp past the field (warp-uniform)
+    const int c = blockIdx.y;
+    const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    extern __shared__ __align__(16) unsigned char zl_smem[];
+    real *dsm = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * COLS + lane * V;
+    ZWalk<real, V, MODE> W;
+    W.init(A, th, grp * COLS + lane * V, lane, j0, j1);
+    const real *__restrict__ zc = A.zc;
+    real dp[V], x[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        const bool in = W.ib + q < Nr;
+        dp[q] = in ? zc[((size_t)c * 2) * Nr + W.ib + q] : real(0);
+        x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + W.ib + q] : real(0);
+    }
+    W.walk(A.ucls[c], A.R, [&](int j, const real(&d)[V], const real(&e)[V][8]) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[q][0], e[q][1] * dp[q]);
+        ZVec<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
+    });
+    // backward from the carry-out; the rows the increments are added to and
+    // the cp values are fetched ZQ rows ahead
+    const real *__restrict__ pkA = A.pkA;
+    auto fetchb = [&](int x0, real (&base)[ZQ][V], real (&cpv)[ZQ][V]) {
+#pragma unroll
+        for (int p = 0; p < ZQ; ++p) {
+            const int j = x0 - p;
+            if (j >= j0) {
+                if constexpr (MODE != MODE_LIT) W.row(th, j, base[p]);
+                if (W.uni) {
+                    const real cv = __ldg(pkA + 4 * ((size_t)W.b[0] * Nz + j) + 2);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) cpv[p][q] = cv;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) cpv[p][q] = __ldg(pkA + 4 * ((size_t)W.b[q] * Nz + j) + 2);
+                }
+            }
+        }
+    };
+    auto procb = [&](int x0, const real (&base)[ZQ][V], const real (&cpv)[ZQ][V]) {
+#pragma unroll
+        for (int p = 0; p < ZQ; ++p) {
+            const int j = x0 - p;
+            if (j >= j0) {
+                real dd[V];
+                {
+                    const real *ps = dsm + (size_t)(j - j0) * COLS;
+                    if constexpr (sizeof(real) == 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(ps);
+                        dd[0] = a.x, dd[1] = a.y, dd[2] = a.z, dd[3] = a.w;
+                    } else {
+                        const double2 a = *reinterpret_cast<const double2 *>(ps);
+                        dd[0] = a.x, dd[1] = a.y;
+                    }
+                }
+                real o[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    x[q] = fmad(cpv[p][q], x[q], dd[q]);
+                    o[q] = MODE == MODE_LIT ? x[q] : base[p][q] + x[q];
+                }
+                if (W.any) {
+                    real *orow = out + (size_t)j * Nr + W.ib;
+                    if (W.vec) {
+                        ZVec<real, V>::st(orow, o);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < V; ++q)
+                            if (W.ib + q < Nr) orow[q] = o[q];
+                    }
+                }
+            }
+        }
+    };
+    {
+        real ba[ZQ][V], ca[ZQ][V], bb[ZQ][V], cb[ZQ][V];
+        fetchb(j1 - 1, ba, ca);
+#pragma unroll 1
+        for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
+            const bool h1 = x0 - ZQ >= j0;
+            if (h1) fetchb(x0 - ZQ, bb, cb);
+            procb(x0, ba, ca);
+            if (h1) {
+                if (x0 - 2 * ZQ >= j0) fetchb(x0 - 2 * ZQ, ba, ca);
+                procb(x0 - ZQ, bb, cb);
+            }
+        }
+    }
+}
+
+// Pass 2: chunk carries.  A block of ZSEG2 warps serves 32 columns (lane =
+// column: every access is coalesced); warp s owns chunks [s m, (s+1) m),
+// m = ceil(nch / ZSEG2) <= ZMAXM, loads all their summaries and constants at
+// once, composes its segment's affine maps, joins the segments through shared
+// memory and writes cin_c = D_{c-1} and xin_c = X_{c+1} to zc[(c*2 + 0|1)*Nr + i].
+constexpr int ZSEG2 = 32;
+constexpr int ZMAXM = 8;
+
+template <typename real>
+__global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<real> *__restrict__ args)
+{
+    const SweepArgs<real> &A = args[blockIdx.y];
+    const int Nr = A.Nr, nch = A.nch;
+    if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
+    const real *__restrict__ zs = A.zs;
+    real *__restrict__ zc = A.zc;
+    __shared__ real sF[ZSEG2][33], sB[ZSEG2][33];
+    const int lane = threadIdx.x & 31, sgm = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const bool col = i < Nr;
+    const real *__restrict__ chb = A.chk + (size_t)(col ? A.colcls[i] : 0) * nch * 4;
+    const int m = (nch + ZSEG2 - 1) / ZSEG2;
+    const int c0 = sgm * m;
+    const size_t st = (size_t)2 * Nr;
+    real Bv[ZMAXM], Gv[ZMAXM], Fv[ZMAXM], Hv[ZMAXM];
+#pragma unroll
+    for (int u = 0; u < ZMAXM; ++u) {
+        const int c = c0 + u;
+        const bool ok = col && u < m && c < nch;
+        Bv[u] = ok ? zs[c * st + i] : real(0);
+        Gv[u] = ok ? zs[c * st + Nr + i] : real(0);
+        Fv[u] = ok ? chb[c * 4] : real(1);
+        Hv[u] = ok ? chb[c * 4 + 1] : real(1);
+    }
+    // forward: D_c = B_c + F_c D_{c-1}
+    real F = real(1), B = real(0);
+#pragma unroll
+    for (int u = 0; u < ZMAXM; ++u) {
+        B = fmad(Fv[u], B, Bv[u]);
+        F *= Fv[u];
+    }
+    sF[sgm][lane] = F;
+    sB[sgm][lane] = B;
+    __syncthreads();
+    real D = real(0);
+    for (int v = 0; v < sgm; ++v) D = fmad(sF[v][lane], D, sB[v][lane]);
+    // Gv becomes G0_c + GP_c D_{c-1}, the backward map's constant term
+#pragma unroll
+    for (int u = 0; u < ZMAXM; ++u) {
+        const int c = c0 + u;
+        const bool ok = col && u < m && c < nch;
+        if (ok) {
+            zc[c * st + i] = D;
+            Gv[u] = fmad(chb[c * 4 + 2], D, Gv[u]);
+        }
+        D = fmad(Fv[u], D, Bv[u]);
+    }
+    // backward: X_c = (G0_c + GP_c D_{c-1}) + H_c X_{c+1}
+    real H = real(1), Gm = real(0);
+#pragma unroll
+    for (int u = ZMAXM - 1; u >= 0; --u) {
+        Gm = fmad(Hv[u], Gm, Gv[u]);
+        H *= Hv[u];
+    }
+    __syncthreads();
+    sF[sgm][lane] = H;
+    sB[sgm][lane] = Gm;
+    __syncthreads();
+    real X = real(0);
+    for (int v = ZSEG2 - 1; v > sgm; --v) X = fmad(sF[v][lane], X, sB[v][lane]);
+#pragma unroll
+    for (int u = ZMAXM - 1; u >= 0; --u) {
+        if (col && u < m && c0 + u < nch) zc[(c0 + u) * st + Nr + i] = X;
+        X = fmad(Hv[u], X, Gv[u]);
+    }
+}
+
+}  // namespace heat

@@ -69,7 +69,8 @@ def test_members_match_their_oracle_runs(precision):
     b.close()
 
 
-@pytest.mark.parametrize("tuning", [(8, 1, 1), (16, 2, 2), (16, 0, 1), (32, 4, 2), (32, 64, 1), (16, 1000, 2)])
+@pytest.mark.parametrize("tuning", [(1, 0, 1), (1, 1, 2), (1, 16, 1), (8, 1, 1), (16, 2, 2), (16, 0, 1), (32, 4, 2),
+                                    (32, 64, 1), (16, 1000, 2)])
 def test_every_schedule_gives_the_same_answer(tuning):
     from paper_1912_03744_gb300 import HeatBatch
     sel = _pick(ENSEMBLE, 3, seed=2)
@@ -77,7 +78,7 @@ def test_every_schedule_gives_the_same_answer(tuning):
     ref, dts = _oracle_runs(probs, 12)
     b = HeatBatch(probs, dts, precision="fp32")
     rK, band, zw = tuning
-    if max(p.Nr for p in probs) > 32 * rK:
+    if rK >= 4 and max(p.Nr for p in probs) > 32 * rK:  # block lines: one line within one warp
         from paper_1912_03744_gb300.heat import HeatError
         with pytest.raises(HeatError):
             b.set_tuning(rK, band, zw)
