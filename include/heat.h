@@ -235,9 +235,10 @@ int heat_batch_tune(heat_batch *b, int trial_steps, double *best_ms);
 
 /* Set or read the schedule.  rK selects the r-sweep: 1 = line teams (a team
  * of lanes walks each r-line, 8 cells per lane in FP32, 4 in FP64; FP64 and
- * FP32 only, lines up to 4096 FP32 / 2048 FP64 cells); 4, 8, 16, 32 = one
- * line per thread group with rK cells per thread; 0 = default (line teams
- * where every member allows them).  band >= 0: rows per line slot (line
+ * FP32 only, lines up to 4096 FP32 / 2048 FP64 cells); 2 = register-resident
+ * lines (FP32 only, 8 cells per thread, lines up to 2048 cells); 4, 8, 16, 32
+ * = one line per thread group with rK cells per thread; 0 = default (2 where
+ * every member allows it, else 1, else 8).  band >= 0: rows per line slot (line
  * teams: rows per team when sizing the grid), 0 = default.  zwpb in
  * {0 (default), 1, 2}.  An invalid combination for these members returns
  * HEAT_ERR_ARG and keeps the current schedule. */

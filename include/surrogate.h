@@ -100,6 +100,26 @@ int surr_infer_checked(surr_ctx *s, const double *params, int B, int n_check, do
  * as the baseline: T [B][Nz][Nr] floats (host or device). */
 int surr_solve(surr_ctx *s, const double *params, int B, float *T, int on_device);
 
+/* Train on n solver fields: params [n][7] (host), T_true [n][Nz][Nr] floats
+ * on the device (e.g. from surr_solve with on_device = 1).  epochs passes
+ * over the data in minibatches of batch <= max_batch samples, each pass in an
+ * order drawn from a splitmix64 stream seeded by seed (Fisher-Yates); one
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8) per minibatch with learning
+ * rate lr0 (lr_min_frac + (1 - lr_min_frac) (1 + cos(pi step / steps)) / 2),
+ * a cosine decay from lr0 to lr_min_frac lr0 over all steps of the call.  last_epoch_loss (may be NULL): the
+ * mean loss over the last pass.  Continues the optimizer state of earlier
+ * calls.  HEAT_ERR_ARG on bad sizes or parameters; HEAT_ERR_NONFINITE if the
+ * loss becomes NaN or Inf. */
+int surr_train(surr_ctx *s, const double *params, int n, const float *T_true, int epochs, int batch,
+               double lr0, double lr_min_frac, unsigned seed, double *last_epoch_loss);
+
+/* The network's error on B samples with known fields T_true [B][Nz][Nr]
+ * (host or device): errs[b] = max |T_net - T_true| / max |T_true - T_init|
+ * over the cells of sample b (the rise-relative max error the fallback of
+ * surr_infer_checked uses). */
+int surr_errors(surr_ctx *s, const double *params, int B, const float *T_true, int true_on_device,
+                double *errs);
+
 void surr_destroy(surr_ctx *s);
 
 #ifdef __cplusplus

@@ -243,6 +243,45 @@ __global__ void head_kernel(const bf16 *__restrict__ h, const double *__restrict
     }
 }
 
+// dst[b][:] = src[idx[b]][:]   (a minibatch of training fields)
+__global__ void gather_rows_kernel(const float *__restrict__ src, const int *__restrict__ idx, int B, long long P,
+                                   float *__restrict__ dst)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < B * P; t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t / P);
+        const long long p = t - b * P;
+        dst[t] = src[(long long)idx[b] * P + p];
+    }
+}
+
+// Per sample b (block b): max |T - Tt| and max |Tt - T_init| -> out[2b], out[2b+1].
+__global__ void err_kernel(const float *__restrict__ T, const float *__restrict__ Tt, long long P, double T_init,
+                           double *__restrict__ out)
+{
+    const int b = blockIdx.x;
+    double e = 0.0, r = 0.0;
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+        const double tt = (double)Tt[(long long)b * P + p];
+        e = fmax(e, fabs((double)T[(long long)b * P + p] - tt));
+        r = fmax(r, fabs(tt - T_init));
+    }
+    __shared__ double se[256], sr[256];
+    se[threadIdx.x] = e;
+    sr[threadIdx.x] = r;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + s]);
+            sr[threadIdx.x] = fmax(sr[threadIdx.x], sr[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * b] = se[0];
+        out[2 * b + 1] = sr[0];
+    }
+}
+
 // out[r] += sum over b, p of src[b][r][p]   (block per (r, chunk))
 __global__ void rowsum_kernel(const bf16 *__restrict__ src, int B, int R, long long P, float *__restrict__ out)
 {
@@ -378,6 +417,8 @@ struct surr_ctx {
     float *dv0 = nullptr;      // [B][C][P]
     float *part = nullptr;     // split-K partials
     float *dWblk = nullptr;    // [NM][2C][2C]
+    int *d_idx = nullptr;      // [max_batch] minibatch sample indices (surr_train)
+    double *d_err = nullptr;   // [2 max_batch] per-sample error maxima (surr_errors)
     size_t part_n = 0;
 };
 
@@ -389,7 +430,7 @@ void free_surr(surr_ctx *s)
     void *bufs[] = {s->w,  s->g,  s->m,    s->v,    s->Wb,   s->Q1b,  s->Q2b, s->Wblk, s->Fr,   s->Gr,
                     s->Fz, s->rn, s->zn,   s->d_params, s->d_loss, s->act, s->pre, s->S,  s->A1,  s->A3,
                     s->P2, s->Yh, s->Xm,   s->Ym,   s->Ymb,  s->hpre, s->h,   s->Tout, s->Ttrue, s->gu,
-                    s->dp0, s->dp1, s->dv0, s->part, s->dWblk};
+                    s->dp0, s->dp1, s->dv0, s->part, s->dWblk, s->d_idx, s->d_err};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete s;
@@ -834,6 +875,8 @@ int surr_create(const surr_dims *dims, const heat_geometry *geom, const heat_mat
     s->part_n = B * kSplit * (size_t)H * (H > C ? H : C);
     A(dalloc(s->part, s->part_n));
     A(dalloc(s->dWblk, (size_t)s->NM * 4 * C * C));
+    A(dalloc(s->d_idx, B));
+    A(dalloc(s->d_err, 2 * B));
     if (e != cudaSuccess) {
         free_surr(s);
         return cuda_status(e);
@@ -1014,6 +1057,99 @@ int surr_infer_checked(surr_ctx *s, const double *params, int B, int n_check, do
     const int fb = worst > tol ? 1 : 0;
     if (used_fallback) *used_fallback = fb;
     if (fb) return solve_batch(s, params, B, T, on_device);
+    return HEAT_OK;
+}
+
+int surr_train(surr_ctx *s, const double *params, int n, const float *T_true, int epochs, int batch, double lr0,
+               double lr_min_frac, unsigned seed, double *last_epoch_loss)
+{
+    if (!s || !params || !T_true || n < 1 || epochs < 1 || batch < 1 || batch > s->max_batch || !(lr0 > 0.0) ||
+        !(lr_min_frac >= 0.0 && lr_min_frac <= 1.0))
+        return HEAT_ERR_ARG;
+    if (!params_ok(params, n)) return HEAT_ERR_ARG;
+    const long long P = s->P;
+    const int per_epoch = (n + batch - 1) / batch;
+    const double total = (double)epochs * per_epoch;
+    std::vector<int> perm(n), idx(batch);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    std::vector<double> hp((size_t)batch * 7);
+    // splitmix64 stream for the per-epoch shuffles
+    unsigned long long state = 0x9e3779b97f4a7c15ULL * ((unsigned long long)seed + 1ULL);
+    auto next = [&]() {
+        unsigned long long z = (state += 0x9e3779b97f4a7c15ULL);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        return z ^ (z >> 31);
+    };
+    double epoch_loss = 0.0;
+    long long step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = n - 1; i > 0; --i) {
+            const int k = (int)(next() % (unsigned long long)(i + 1));
+            const int t = perm[i];
+            perm[i] = perm[k];
+            perm[k] = t;
+        }
+        SURR_TRY(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
+        for (int b0 = 0; b0 < n; b0 += batch) {
+            const int B = n - b0 < batch ? n - b0 : batch;
+            for (int b = 0; b < B; ++b) {
+                idx[b] = perm[b0 + b];
+                std::memcpy(&hp[(size_t)b * 7], params + 7 * (size_t)idx[b], 7 * sizeof(double));
+            }
+            SURR_TRY(cudaMemcpyAsync(s->d_params, hp.data(), (size_t)B * 7 * sizeof(double), cudaMemcpyHostToDevice,
+                                     s->stream));
+            SURR_TRY(cudaMemcpyAsync(s->d_idx, idx.data(), (size_t)B * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+            gather_rows_kernel<<<grid_for((long long)B * P), 256, 0, s->stream>>>(T_true, s->d_idx, B, P, s->Ttrue);
+            SURR_TRY(cudaGetLastError());
+            SURR_TRY(cudaMemsetAsync(s->g, 0, s->n_params * sizeof(float), s->stream));
+            SURR_TRY(forward_chunk(s, B, true, s->Ttrue, s->Tout));
+            SURR_TRY(backward_chunk(s, B));
+            const double lr = lr0 * (lr_min_frac + (1.0 - lr_min_frac) * 0.5 * (1.0 + std::cos(kPiD * step / total)));
+            s->adam_t += 1;
+            const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, s->adam_t)));
+            const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, s->adam_t)));
+            adam_kernel<<<grid_for((long long)s->n_params), 256, 0, s->stream>>>(
+                (long long)s->n_params, s->w, s->g, s->m, s->v, (float)lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+            SURR_TRY(cudaGetLastError());
+            SURR_TRY(refresh(s));
+            ++step;
+        }
+        double l = 0.0;
+        SURR_TRY(cudaMemcpyAsync(&l, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        SURR_TRY(cudaStreamSynchronize(s->stream));
+        // each minibatch adds its squared-error sum scaled by 1 (head_kernel), so the mean is over all cells
+        epoch_loss = l / ((double)n * P);
+        if (!std::isfinite(epoch_loss)) return HEAT_ERR_NONFINITE;
+    }
+    if (last_epoch_loss) *last_epoch_loss = epoch_loss;
+    return HEAT_OK;
+}
+
+int surr_errors(surr_ctx *s, const double *params, int B, const float *T_true, int true_on_device, double *errs)
+{
+    if (!s || !params || !T_true || !errs || B < 1) return HEAT_ERR_ARG;
+    if (!params_ok(params, B)) return HEAT_ERR_ARG;
+    const long long P = s->P;
+    std::vector<double> e2((size_t)2 * s->max_batch);
+    for (int b0 = 0; b0 < B; b0 += s->max_batch) {
+        const int n = B - b0 < s->max_batch ? B - b0 : s->max_batch;
+        int st = upload_params(s, params + 7 * (size_t)b0, n);
+        if (st != HEAT_OK) return st;
+        const float *Tt = T_true + (size_t)b0 * P;
+        if (!true_on_device) {
+            SURR_TRY(cudaMemcpyAsync(s->Ttrue, Tt, (size_t)n * P * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+            Tt = s->Ttrue;
+        }
+        SURR_TRY(forward_chunk(s, n, false, nullptr, s->Tout));
+        err_kernel<<<n, 256, 0, s->stream>>>(s->Tout, Tt, P, s->T_init, s->d_err);
+        SURR_TRY(cudaGetLastError());
+        SURR_TRY(cudaMemcpyAsync(e2.data(), s->d_err, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s->stream));
+        SURR_TRY(cudaStreamSynchronize(s->stream));
+        for (int b = 0; b < n; ++b)
+            errs[b0 + b] = e2[2 * b + 1] > 0.0 ? e2[2 * b] / e2[2 * b + 1] : (e2[2 * b] > 0.0 ? INFINITY : 0.0);
+    }
     return HEAT_OK;
 }
 

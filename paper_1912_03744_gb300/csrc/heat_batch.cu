@@ -217,7 +217,7 @@ int heat_batch_sync(heat_batch *b)
 int heat_batch_set_tuning(heat_batch *b, int rK, int band, int zwpb)
 {
     if (!b || rK < 0 || band < 0 || band > 4096 || zwpb < 0 || zwpb > 2) return HEAT_ERR_ARG;
-    if (rK != 0 && rK != 1 && rK != 4 && rK != 8 && rK != 16 && rK != 32) return HEAT_ERR_ARG;
+    if (rK != 0 && rK != 1 && rK != 2 && rK != 4 && rK != 8 && rK != 16 && rK != 32) return HEAT_ERR_ARG;
     Tuning t;
     t.rK = rK;
     t.band = band;
@@ -272,13 +272,14 @@ int heat_batch_tune(heat_batch *b, int trial_steps, double *best_ms)
     const Tuning start = b->plan.used;
     Tuning best = start;
     float best_t = -1.f;
-    const int Ks[] = {1, 4, 8, 16, 32};  // 1: line-team r-sweep
+    const int Ks[] = {1, 2, 4, 8, 16, 32};  // 1: line teams, 2: register-resident lines
     const int bands[] = {0, 1, 2, 4, 8, 16, 32};
     for (int K : Ks)
         for (int band : bands)
             for (int w = 1; w <= 2 && e == cudaSuccess; ++w) {
                 if (b->precision != HEAT_FP64 && K == 4) continue;
                 if (K == 1 && band > 16) continue;
+                if (K == 2 && band == 1) continue;
                 Tuning t;
                 t.rK = K;
                 t.band = band;

@@ -58,6 +58,7 @@ __device__ __forceinline__ double fmad(double a, double b, double c) { return __
 }  // namespace heat
 
 #include "heat_rline.cuh"
+#include "heat_rblock.cuh"
 #include "heat_zline.cuh"
 
 namespace heat {
@@ -1355,6 +1356,70 @@ static cudaError_t plan_rline(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
     return cudaSuccess;
 }
 
+// Register-resident r-sweep (heat_rblock.cuh; FP32 increment form, K = 8
+// cells per thread, lines of up to 2048 cells): G = the power of two >= Nr/8
+// threads per line (at least 4), 256/G line slots per block, each slot walking
+// `band` rows.  One instance: the band that fills every resident block slot
+// once; a batch: the largest band that still gives two waves.
+constexpr int kRBlockK = 8, kRBlockRing = 8;
+
+static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
+{
+    constexpr int K = kRBlockK;
+    for (int m = 0; m < n; ++m) {
+        if (h[m].Nr > 256 * K) return cudaErrorInvalidValue;
+        int G = 4;
+        while (G * K < h[m].Nr) G <<= 1;
+        h[m].G = G;
+    }
+    const void *fn = (const void *)rblock_kernel<K, kRBlockRing>;
+    const int block = 256;
+    const size_t smem = (size_t)kRBlockRing * block * K * sizeof(float);
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem)) != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    auto blocks_for = [&](int band, long long *tot) {
+        int mx = 1;
+        *tot = 0;
+        for (int m = 0; m < n; ++m) {
+            const int lpb = block / h[m].G;
+            const int bx = ((h[m].Nz + band - 1) / band + lpb - 1) / lpb;
+            *tot += bx;
+            mx = bx > mx ? bx : mx;
+        }
+        return mx;
+    };
+    int band = tu.band;
+    if (band <= 0) {
+        if (n == 1) {
+            const int lpb = block / h[0].G;
+            const long long slots = (long long)kSMs * per_sm * lpb;
+            band = (int)((h[0].Nz + slots - 1) / slots);
+            band = band < 2 ? 2 : band;
+        } else {
+            band = 2;
+            for (int b = 64; b > 2; b >>= 1) {
+                long long tot;
+                blocks_for(b, &tot);
+                if (tot >= 2LL * kSMs * per_sm) { band = b; break; }
+            }
+        }
+    }
+    long long tot;
+    const int gx = blocks_for(band, &tot);
+    for (int m = 0; m < n; ++m) h[m].band = band;
+    tu.band = band;
+    tu.rK = 2;
+    L.fn = fn;
+    L.grid = dim3(gx, n, 1);
+    L.block = dim3(block, 1, 1);
+    L.smem = smem;
+    L.flip = true;
+    return cudaSuccess;
+}
+
 template <typename real, int MODE>
 static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
@@ -1400,7 +1465,7 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     a.fn = lean ? (const void *)zsum2_kernel<real, V, lean ? MODE : MODE_DELTA> : (const void *)zsum_kernel<real, V, MODE>;
     a.grid = dim3((groups + SWPB - 1) / SWPB, maxNch, n);
     a.block = dim3(32 * SWPB, 1, 1);
-    a.smem = lean ? 0 : (size_t)SWPB * maxRc * 8 * sizeof(real);
+    a.smem = (size_t)SWPB * maxRc * 8 * sizeof(real);
     a.flip = true;
     cudaError_t e = allow_smem(a.fn, a.smem);
     if (e != cudaSuccess) return e;
@@ -1417,7 +1482,7 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
                 : (const void *)zsolve_kernel<real, V, MODE>;
     c.grid = dim3((groups + wpb - 1) / wpb, maxNch, n);
     c.block = dim3(32 * wpb, 1, 1);
-    c.smem = lean ? (size_t)wpb * maxRc * COLS * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
+    c.smem = (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
     c.flip = true;
     if ((e = allow_smem(c.fn, c.smem)) != cudaSuccess) return e;
     out.push_back(a);
@@ -1436,13 +1501,24 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     cudaError_t e = cudaErrorInvalidValue;
     bool line_tables = MODE == MODE_LIT || MODE == MODE_DELTA;
     for (int m = 0; m < n && line_tables; ++m) line_tables = h[m].rl.tA != nullptr;
+    // rK: 0 = default, 1 = line teams, 2 = register-resident lines (FP32
+    // increment form), 4..32 = block lines with rK cells per thread
+    if constexpr (MODE == MODE_DELTA && sizeof(real) == 4) {
+        if (tu.rK == 0 || tu.rK == 2) {
+            e = plan_rblock(h, n, tu, r);
+            if (e != cudaSuccess && tu.rK == 2) return e;
+        }
+    } else {
+        if (tu.rK == 2) return cudaErrorInvalidValue;
+    }
     if constexpr (MODE == MODE_LIT || MODE == MODE_DELTA) {
-        // rK: 0 = line teams where possible, 1 = line teams, 4..32 = block lines
-        if (tu.rK == 1 && !line_tables) return cudaErrorInvalidValue;
-        if (tu.rK <= 1 && line_tables) e = plan_rline<real, MODE>(h, n, tu, r);
+        if (e == cudaErrorInvalidValue) {
+            if (tu.rK == 1 && !line_tables) return cudaErrorInvalidValue;
+            if (tu.rK <= 1 && line_tables) e = plan_rline<real, MODE>(h, n, tu, r);
+        }
     }
     if (e == cudaErrorInvalidValue) {
-        if (tu.rK == 1) tu.rK = 0;
+        if (tu.rK <= 2) tu.rK = 0;
         e = plan_rsweep<real, MODE>(h, n, tu, r);
     }
     if (e != cudaSuccess) return e;

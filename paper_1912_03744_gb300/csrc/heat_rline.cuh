@@ -206,34 +206,18 @@ __global__ void __launch_bounds__(128) rline_kernel(const SweepArgs<real> *__res
                 if (rin[q]) IO::load(rowp[q], i0, Nr, vec, (q >= 1 && q <= R) ? bc1 : real(0), x[q]);
                 else IO::fill(q == 0 ? bc2 : bc3, x[q]);
             }
-            // z coefficients of each row for each cell
+            // z coefficients of each row: one value per row for a chunk inside one
+            // column class (the chunk's first cell's class otherwise; the cells of
+            // another class are redone below)
             const int zc = RL.zcl[c];
-            real zm[R][K], zp[R][K], zd[R][K], zs[R][K];
-            if (zc >= 0) {
+            const int zc0 = zc >= 0 ? zc : (i0 < Nr ? colcls[i0] : 0);
+            real zm[R], zp[R], zd[R], zs[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const size_t zo = (size_t)zc * Nz + min(j0 + r, Nz - 1);
-                    real v0, v1, v2 = real(0), v3 = real(0);
-                    if constexpr (LIT) v0 = Z.am[zo], v1 = Z.ap[zo], v2 = Z.ad[zo], v3 = Z.sd[zo];
-                    else v0 = Z.xm[zo], v1 = Z.xp[zo];
-#pragma unroll
-                    for (int k = 0; k < K; ++k) zm[r][k] = v0, zp[r][k] = v1, zd[r][k] = v2, zs[r][k] = v3;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int cc = i0 + k < Nr ? colcls[i0 + k] : -1;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const size_t zo = (size_t)(cc < 0 ? 0 : cc) * Nz + min(j0 + r, Nz - 1);
-                        real v0 = real(0), v1 = real(0), v2 = real(0), v3 = real(0);
-                        if (cc >= 0) {
-                            if constexpr (LIT) v0 = Z.am[zo], v1 = Z.ap[zo], v2 = Z.ad[zo], v3 = Z.sd[zo];
-                            else v0 = Z.xm[zo], v1 = Z.xp[zo];
-                        }
-                        zm[r][k] = v0, zp[r][k] = v1, zd[r][k] = v2, zs[r][k] = v3;
-                    }
-                }
+            for (int r = 0; r < R; ++r) {
+                const size_t zo = (size_t)zc0 * Nz + min(j0 + r, Nz - 1);
+                zd[r] = zs[r] = real(0);
+                if constexpr (LIT) zm[r] = Z.am[zo], zp[r] = Z.ap[zo], zd[r] = Z.ad[zo], zs[r] = Z.sd[zo];
+                else zm[r] = Z.xm[zo], zp[r] = Z.xp[zo];
             }
             // right neighbour of the last cell of the lane: next lane's first cell,
             // for the team's last lane the next segment's first cell (or the ghost)
@@ -249,6 +233,22 @@ __global__ void __launch_bounds__(128) rline_kernel(const SweepArgs<real> *__res
                     left[r] = __shfl_sync(FULL, x[r + 1][K - 1], LW - 1, LW);
                 }
             }
+            // right-hand side of cell k of row r with z coefficients (y0..y3)
+            auto rhs = [&](int r, int k, real a0, real a1, real a2, real y0, real y1, real y2, real y3) {
+                const real xc = x[r + 1][k];
+                if constexpr (LIT) {
+                    // {w, s, -, inv}: (w + ad_z) x + am_z x_{j-1} + ap_z x_{j+1} + s + sd_z
+                    return fmad(a0 + y2, xc, fmad(y0, x[r][k], fmad(y1, x[r + 2][k], a1 + y3)));
+                } else {
+                    // {xm, xp, q, inv}: every coupling applied to a difference
+                    const real l = k > 0 ? x[r + 1][k - 1] : nl_[r];
+                    const real rr = k < K - 1 ? x[r + 1][k + 1] : nr_[r];
+                    real v = fmad(a0, l - xc, a2);
+                    v = fmad(a1, rr - xc, v);
+                    v = fmad(y0, x[r][k] - xc, v);
+                    return fmad(y1, x[r + 2][k] - xc, v);
+                }
+            };
             real d[R][K], iv[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -256,19 +256,26 @@ __global__ void __launch_bounds__(128) rline_kernel(const SweepArgs<real> *__res
                 rl_ld4(tA + (size_t)(i0 + k) * 4, a0, a1, a2, a3);
                 iv[k] = a3;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const real xc = x[r + 1][k];
-                    if constexpr (LIT) {
-                        // {w, s, -, inv}: (w + ad_z) x + am_z x_{j-1} + ap_z x_{j+1} + s + sd_z
-                        d[r][k] = fmad(a0 + zd[r][k], xc, fmad(zm[r][k], x[r][k], fmad(zp[r][k], x[r + 2][k], a1 + zs[r][k])));
-                    } else {
-                        // {xm, xp, q, inv}: every coupling applied to a difference
-                        const real l = k > 0 ? x[r + 1][k - 1] : nl_[r];
-                        const real rr = k < K - 1 ? x[r + 1][k + 1] : nr_[r];
-                        real v = fmad(a0, l - xc, a2);
-                        v = fmad(a1, rr - xc, v);
-                        v = fmad(zm[r][k], x[r][k] - xc, v);
-                        d[r][k] = fmad(zp[r][k], x[r + 2][k] - xc, v);
+                for (int r = 0; r < R; ++r) d[r][k] = rhs(r, k, a0, a1, a2, zm[r], zp[r], zd[r], zs[r]);
+            }
+            if (zc < 0) {
+                // a chunk across a column-class boundary (layer interface): the
+                // cells of another class again, with their own z coefficients
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int i = i0 + k;
+                    const int cc = i < Nr ? colcls[i] : zc0;
+                    if (cc != zc0) {
+                        real a0, a1, a2, a3;
+                        rl_ld4(tA + (size_t)i * 4, a0, a1, a2, a3);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const size_t zo = (size_t)cc * Nz + min(j0 + r, Nz - 1);
+                            real y0, y1, y2 = real(0), y3 = real(0);
+                            if constexpr (LIT) y0 = Z.am[zo], y1 = Z.ap[zo], y2 = Z.ad[zo], y3 = Z.sd[zo];
+                            else y0 = Z.xm[zo], y1 = Z.xp[zo];
+                            d[r][k] = rhs(r, k, a0, a1, a2, y0, y1, y2, y3);
+                        }
                     }
                 }
             }

@@ -86,6 +86,8 @@ struct ZWalk {
     real ra[V], rb[V], rc[V], rd[V];  // increment: xm, xp of the row class; literal: am, ap, ad, sd
     real bz_lo, bz_hi, br_lo, br_hi;  // ghost values beyond the outer faces
     real tm[V], t[V];                 // rows j-1 and j of the walk
+    const real *stg = nullptr;        // the chunk's staged table rows [j1 - j0][8] (uniform warps)
+    int bw = 0;                       // the warp's column class when it has one
 
     __device__ __forceinline__ void init(const SweepArgs<real> &A, const real *th_, int ib_, int lane_, int j0_,
                                          int j1_)
@@ -163,23 +165,60 @@ struct ZWalk {
             }
         }
     }
-    // table values of row j for each column
-    __device__ __forceinline__ void tab(int j, real (&e)[V][8]) const
+    // True (for every lane) when every column of the warp inside the field has
+    // lane 0's column class bw; lanes past the field then compute with bw too
+    // and store nothing.
+    __device__ __forceinline__ bool warp_uniform()
     {
-        if (uni) {
-            real s8[8];
-            zl_tab(pkA, pkB, (size_t)b[0] * Nz + j, s8);
+        bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
+        return __all_sync(HEAT_FULL_MASK, !any || (uni && b[0] == bw));
+    }
+    // Stage the chunk's table rows of class bw (a uniform warp) in the warp's
+    // shared-memory slice buf [j1 - j0][8]: one row per lane per pass, all
+    // loads in flight together.
+    __device__ __forceinline__ void stage(real *buf)
+    {
+        for (int r = lane; r < j1 - j0; r += 32) {
+            real e[8];
+            zl_tab(pkA, pkB, (size_t)bw * Nz + j0 + r, e);
+            real *d = buf + (size_t)r * 8;
+            if constexpr (sizeof(real) == 4) {
+                *reinterpret_cast<float4 *>(d) = make_float4(e[0], e[1], e[2], e[3]);
+                *reinterpret_cast<float4 *>(d + 4) = make_float4(e[4], e[5], e[6], e[7]);
+            } else {
 #pragma unroll
-            for (int q = 0; q < V; ++q)
+                for (int u = 0; u < 8; u += 2) *reinterpret_cast<double2 *>(d + u) = make_double2(e[u], e[u + 1]);
+            }
+        }
+        __syncwarp();
+        stg = buf;
+    }
+    // table values of row j: E = 1 (every column of the warp shares one class:
+    // the staged rows) or E = V (per column, from the read-only cache)
+    template <int E>
+    __device__ __forceinline__ void tab(int j, real (&e)[E][8]) const
+    {
+        if constexpr (E == 1) {
+            const real *p = stg + (size_t)(j - j0) * 8;
+            if constexpr (sizeof(real) == 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(p), c = *reinterpret_cast<const float4 *>(p + 4);
+                e[0][0] = a.x, e[0][1] = a.y, e[0][2] = a.z, e[0][3] = a.w;
+                e[0][4] = c.x, e[0][5] = c.y, e[0][6] = c.z, e[0][7] = c.w;
+            } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) e[q][u] = s8[u];
+                for (int u = 0; u < 8; u += 2) {
+                    const double2 a = *reinterpret_cast<const double2 *>(p + u);
+                    e[0][u] = a.x, e[0][u + 1] = a.y;
+                }
+            }
         } else {
 #pragma unroll
-            for (int q = 0; q < V; ++q) zl_tab(pkA, pkB, (size_t)b[q] * Nz + j, e[q]);
+            for (int q = 0; q < E; ++q) zl_tab(pkA, pkB, (size_t)b[q] * Nz + j, e[q]);
         }
     }
-    // right-hand side of row j (then advance the row window): e[q] = table row of column q
-    __device__ __forceinline__ void rhs(int j, const Group &G, int p, const real (&e)[V][8], real (&d)[V])
+    // right-hand side of row j (then advance the row window)
+    template <int E>
+    __device__ __forceinline__ void rhs(const Group &G, int p, const real (&e)[E][8], real (&d)[V])
     {
         real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
         real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
@@ -189,16 +228,17 @@ struct ZWalk {
         if (hi_edge) tr = br_hi;
 #pragma unroll
         for (int q = 0; q < V; ++q) {
+            const real(&eq)[8] = e[E == 1 ? 0 : q];
             const real x = t[q];
             const real l = q > 0 ? t[q - 1] : tl;
             const real r = q < V - 1 ? t[q + 1] : tr;
             if constexpr (LIT) {
                 // e0 = s, e1 = w: (w + ad_r) x + am_r x_{i-1} + ap_r x_{i+1} + s + sd_r
-                d[q] = fmad(e[q][4] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, e[q][3] + rd[q])));
+                d[q] = fmad(eq[4] + rc[q], x, fmad(ra[q], l, fmad(rb[q], r, eq[3] + rd[q])));
             } else {
                 // e0 = q, e1 = xm_z, e2 = xp_z
-                real v = fmad(e[q][4], tm[q] - x, e[q][3]);
-                v = fmad(e[q][5], G.nx[p][q] - x, v);
+                real v = fmad(eq[4], tm[q] - x, eq[3]);
+                v = fmad(eq[5], G.nx[p][q] - x, v);
                 v = fmad(ra[q], l - x, v);
                 d[q] = fmad(rb[q], r - x, v);
             }
@@ -207,8 +247,8 @@ struct ZWalk {
         for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = G.nx[p][q];
     }
     // Walk rows [j0, j1) calling emit(j, d, e) with the right-hand side d of
-    // row j and its table values e.
-    template <typename Emit>
+    // row j and its table values e (E = 1: shared by the lane's columns).
+    template <int E, typename Emit>
     __device__ __forceinline__ void walk(int ucls, const LineTab<real> &R, Emit emit)
     {
         row(th, j0 - 1, tm);
@@ -221,9 +261,9 @@ struct ZWalk {
                 const int j = x + p;
                 if (j < j1) {
                     if (ucls < 0) row_class(rowcls[j], R);
-                    real e[V][8], d[V];
-                    tab(j, e);
-                    rhs(j, G, p, e, d);
+                    real e[E][8], d[V];
+                    tab<E>(j, e);
+                    rhs<E>(G, p, e, d);
                     emit(j, d, e);
                 }
             }
@@ -260,13 +300,21 @@ __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__res
     real sb[V], sg[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) sb[q] = sg[q] = real(0);
-    W.walk(A.ucls[c], A.R, [&](int, const real(&d)[V], const real(&e)[V][8]) {
+    auto emit = [&](int, const real(&d)[V], const auto &e) {
+        constexpr int E = sizeof(e) / sizeof(e[0]);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            sb[q] = fmad(d[q], e[q][6], sb[q]);
-            sg[q] = fmad(d[q], e[q][7], sg[q]);
+            sb[q] = fmad(d[q], e[E == 1 ? 0 : q][6], sb[q]);
+            sg[q] = fmad(d[q], e[E == 1 ? 0 : q][7], sg[q]);
         }
-    });
+    };
+    extern __shared__ __align__(16) unsigned char zs_smem[];
+    if (W.warp_uniform()) {
+        W.stage(reinterpret_cast<real *>(zs_smem) + (size_t)(threadIdx.x >> 5) * Rc * 8);
+        W.template walk<1>(A.ucls[c], A.R, emit);
+    } else {
+        W.template walk<V>(A.ucls[c], A.R, emit);
+    }
     real *__restrict__ zs = A.zs;
     if (W.vec) {
         if (W.any) {
@@ -300,7 +348,9 @@ __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__re
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
     extern __shared__ __align__(16) unsigned char zl_smem[];
-    real *dsm = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * COLS + lane * V;
+    // per warp: forward results [Rc][COLS], then the staged table rows [Rc][8]
+    real *wsm = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * (COLS + 8);
+    real *dsm = wsm + lane * V;
     ZWalk<real, V, MODE> W;
     W.init(A, th, grp * COLS + lane * V, lane, j0, j1);
     const real *__restrict__ zc = A.zc;
@@ -311,11 +361,19 @@ __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__re
         dp[q] = in ? zc[((size_t)c * 2) * Nr + W.ib + q] : real(0);
         x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + W.ib + q] : real(0);
     }
-    W.walk(A.ucls[c], A.R, [&](int j, const real(&d)[V], const real(&e)[V][8]) {
+    auto emit = [&](int j, const real(&d)[V], const auto &e) {
+        constexpr int E = sizeof(e) / sizeof(e[0]);
 #pragma unroll
-        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[q][0], e[q][1] * dp[q]);
+        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dp[q]);
         ZVec<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
-    });
+    };
+    const bool wuni = W.warp_uniform();
+    if (wuni) {
+        W.stage(wsm + (size_t)Rc * COLS);
+        W.template walk<1>(A.ucls[c], A.R, emit);
+    } else {
+        W.template walk<V>(A.ucls[c], A.R, emit);
+    }
     // backward from the carry-out; the rows the increments are added to and
     // the cp values are fetched ZQ rows ahead
     const real *__restrict__ pkA = A.pkA;
@@ -325,8 +383,8 @@ __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__re
             const int j = x0 - p;
             if (j >= j0) {
                 if constexpr (MODE != MODE_LIT) W.row(th, j, base[p]);
-                if (W.uni) {
-                    const real cv = __ldg(pkA + 4 * ((size_t)W.b[0] * Nz + j) + 2);
+                if (wuni) {
+                    const real cv = W.stg[(size_t)(j - j0) * 8 + 2];
 #pragma unroll
                     for (int q = 0; q < V; ++q) cpv[p][q] = cv;
                 } else {

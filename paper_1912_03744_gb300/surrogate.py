@@ -9,7 +9,8 @@ import numpy as np
 from .heat import HEAT_OK, HeatError, _Options, _current_stream_handle, _marshal, load
 
 SURR_SYMBOLS = ["surr_create", "surr_n_params", "surr_set_params", "surr_get_params", "surr_forward",
-                "surr_loss_grad", "surr_adam", "surr_infer_checked", "surr_solve", "surr_destroy"]
+                "surr_loss_grad", "surr_adam", "surr_infer_checked", "surr_solve", "surr_train", "surr_errors",
+                "surr_destroy"]
 
 
 class _Dims(ctypes.Structure):
@@ -38,6 +39,9 @@ def _lib():
         L.surr_infer_checked.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint, fp,
                                          ctypes.c_int, ip, dp]
         L.surr_solve.argtypes = [vp, dp, ctypes.c_int, fp, ctypes.c_int]
+        L.surr_train.argtypes = [vp, dp, ctypes.c_int, fp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_uint, dp]
+        L.surr_errors.argtypes = [vp, dp, ctypes.c_int, fp, ctypes.c_int, dp]
         L.surr_destroy.argtypes = [vp]
         L.surr_destroy.restype = None
         _bound = True
@@ -146,6 +150,27 @@ class Surrogate:
                                                                int(seed), ptr, dev, ctypes.byref(fb),
                                                                ctypes.byref(err)))
         return out, bool(fb.value), err.value
+
+    def train(self, params, fields, epochs, batch, lr, lr_min_frac=0.02, seed=0):
+        """surr_train: fields is a CUDA float32 tensor [n, Nz, Nr]; returns the last epoch's mean loss."""
+        p, pp = self._params(params)
+        assert hasattr(fields, "is_cuda") and fields.is_cuda and fields.dtype.is_floating_point
+        ptr, _ = _ptr(fields)
+        loss = ctypes.c_double()
+        _check("surr_train", _lib().surr_train(self._h, pp, len(p), ptr, int(epochs), int(batch), float(lr),
+                                               float(lr_min_frac), int(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def errors(self, params, fields):
+        """surr_errors: per-sample rise-relative max error of the network against fields."""
+        p, pp = self._params(params)
+        if not (hasattr(fields, "is_cuda") and fields.is_cuda):
+            fields = np.ascontiguousarray(fields, dtype=np.float32)
+        ptr, dev = _ptr(fields)
+        out = np.empty(len(p), dtype=np.float64)
+        _check("surr_errors", _lib().surr_errors(self._h, pp, len(p), ptr, dev,
+                                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
 
     def solve(self, params, out=None):
         p, pp = self._params(params)

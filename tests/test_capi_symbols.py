@@ -37,7 +37,7 @@ def test_binding_symbol_list_matches_header():
 def test_surrogate_symbols_exported_and_bound(lib):
     from paper_1912_03744_gb300.surrogate import SURR_SYMBOLS
     names = _declared("surrogate.h")
-    assert sorted(SURR_SYMBOLS) == names and len(names) == 10
+    assert sorted(SURR_SYMBOLS) == names and len(names) == 12
     for n in names:
         assert hasattr(lib, n), n
 

@@ -69,7 +69,7 @@ def test_members_match_their_oracle_runs(precision):
     b.close()
 
 
-@pytest.mark.parametrize("tuning", [(1, 0, 1), (1, 1, 2), (1, 16, 1), (8, 1, 1), (16, 2, 2), (16, 0, 1), (32, 4, 2),
+@pytest.mark.parametrize("tuning", [(2, 0, 1), (2, 4, 2), (2, 64, 1), (1, 0, 1), (1, 1, 2), (1, 16, 1), (8, 1, 1), (16, 2, 2), (16, 0, 1), (32, 4, 2),
                                     (32, 64, 1), (16, 1000, 2)])
 def test_every_schedule_gives_the_same_answer(tuning):
     from paper_1912_03744_gb300 import HeatBatch
