@@ -24,6 +24,17 @@ namespace heat {
 
 constexpr double kPi = 3.14159265358979323846;
 
+#ifdef __CUDACC__
+// Programmatic dependent launch: the sweep kernels are launched so that a
+// kernel may start while its predecessor in the stream finishes.  Each
+// kernel lets its successor be scheduled at once (launch_dependents) and,
+// before it touches anything a predecessor writes (the fields, the z-pass
+// scratch), waits until the predecessor grid has completed and its writes are
+// visible (wait).  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+#endif
+
 // One direction's per-class tables, structure of arrays, [n_class][N].
 //   inv, f, cp : factorization of the implicit line matrix
 //                -m_i x_{i-1} + b_i x_i - p_i x_{i+1} = d_i  (m, p >= 0):

@@ -264,6 +264,8 @@ __device__ __forceinline__ void solve_row(real (&d)[K], const real (&inv)[K], co
 template <typename real, int K, int MODE, int LB, int NRING>
 __global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.y];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;
@@ -812,6 +814,8 @@ __device__ __forceinline__ void z_walk(ZLane<real, V, MODE> &L, const real *__re
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(128, 4) zsum_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.z];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     const real *__restrict__ rho = MODE == MODE_CORR ? A.rho : nullptr;
@@ -870,6 +874,8 @@ constexpr int ZSEG = 8;
 template <typename real>
 __global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(const SweepArgs<real> *__restrict__ args)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.y];
     const int Nr = A.Nr, nch = A.nch;
     if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
@@ -928,6 +934,8 @@ __global__ void __launch_bounds__(32 * ZSEG) zcarry_kernel(const SweepArgs<real>
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(64, 8) zsolve_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.z];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     const int nwl = G >> 5;  // warps per wide line
     const bool wide = G > 32;
     const int jstart = (blockIdx.x * lpb + slot) * band;
+    pdl_launch_dependents();
     if ((int)blockIdx.x * lpb * band >= Nz) return;  // past this instance (block-uniform)
     const int jend = min(Nz, jstart + band);  // rows this slot stores: [jstart, jend)
     const int i0 = g * K;
@@ -106,15 +107,16 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         }
         rb_commit();
     };
-    // prologue: rows jstart-1 .. jstart+NRING-2
-    for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
-
     // column class of the thread's cells: one for all K, or per cell (a chunk
     // across a layer interface)
     const int zc0 = i0 < Nr ? colcls[i0] : 0;
     bool zuni = true;
 #pragma unroll
     for (int k = 1; k < K; ++k) zuni = zuni && (i0 + k >= Nr || colcls[i0 + k] == zc0);
+
+    pdl_wait();
+    // prologue: rows jstart-1 .. jstart+NRING-2
+    for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
 
     // class state
     int acls = -1;

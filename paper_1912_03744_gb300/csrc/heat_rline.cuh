@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(128) rline_kernel(const SweepArgs<real> *__res
     static_assert(MODE == MODE_LIT || MODE == MODE_DELTA, "the line kernel runs the literal and increment forms");
     using IO = RLineIO<real, K>;
     constexpr bool LIT = MODE == MODE_LIT;
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.y];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;

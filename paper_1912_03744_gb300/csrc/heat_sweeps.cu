@@ -99,12 +99,25 @@ cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPla
     }
 }
 
-// Enqueue one half-step of a plan.  flip = 0 reads f0 and writes f1.
+// Enqueue one half-step of a plan.  flip = 0 reads f0 and writes f1.  Every
+// sweep kernel is launched with programmatic stream serialization (see
+// pdl_wait in heat_internal.h), so its blocks can be scheduled while the
+// previous kernel in the stream drains.
 cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s)
 {
     for (const Launch &L : plan.dir[dir]) {
         void *kargs[2] = {(void *)&d_args, (void *)&flip};
-        cudaError_t e = cudaLaunchKernel(L.fn, L.grid, L.block, kargs, L.smem, s);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = L.grid;
+        cfg.blockDim = L.block;
+        cfg.dynamicSmemBytes = L.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, kargs);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -287,6 +287,7 @@ struct ZWalk {
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    pdl_launch_dependents();
     const SweepArgs<real> &A = args[blockIdx.z];
     const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     if ((int)blockIdx.y >= A.nch) return;
@@ -311,8 +312,10 @@ __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__res
     extern __shared__ __align__(16) unsigned char zs_smem[];
     if (W.warp_uniform()) {
         W.stage(reinterpret_cast<real *>(zs_smem) + (size_t)(threadIdx.x >> 5) * Rc * 8);
+        pdl_wait();
         W.template walk<1>(A.ucls[c], A.R, emit);
     } else {
+        pdl_wait();
         W.template walk<V>(A.ucls[c], A.R, emit);
     }
     real *__restrict__ zs = A.zs;
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__res
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
+    pdl_launch_dependents();
     const SweepArgs<real> &A = args[blockIdx.z];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;
@@ -353,6 +357,9 @@ __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__re
     real *dsm = wsm + lane * V;
     ZWalk<real, V, MODE> W;
     W.init(A, th, grp * COLS + lane * V, lane, j0, j1);
+    const bool wuni = W.warp_uniform();
+    if (wuni) W.stage(wsm + (size_t)Rc * COLS);
+    pdl_wait();
     const real *__restrict__ zc = A.zc;
     real dp[V], x[V];
 #pragma unroll
@@ -367,13 +374,8 @@ __global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__re
         for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dp[q]);
         ZVec<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
     };
-    const bool wuni = W.warp_uniform();
-    if (wuni) {
-        W.stage(wsm + (size_t)Rc * COLS);
-        W.template walk<1>(A.ucls[c], A.R, emit);
-    } else {
-        W.template walk<V>(A.ucls[c], A.R, emit);
-    }
+    if (wuni) W.template walk<1>(A.ucls[c], A.R, emit);
+    else W.template walk<V>(A.ucls[c], A.R, emit);
     // backward from the carry-out; the rows the increments are added to and
     // the cp values are fetched ZQ rows ahead
     const real *__restrict__ pkA = A.pkA;
@@ -456,6 +458,8 @@ constexpr int ZMAXM = 8;
 template <typename real>
 __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<real> *__restrict__ args)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.y];
     const int Nr = A.Nr, nch = A.nch;
     if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
