@@ -227,6 +227,121 @@ def time_ensemble(steps, warmup, precision="fp32", tuning=None):
     return out
 
 
+def time_config4(steps, warmup):
+    """Precision stress at full size: 8192 x 16384 (134 M cells), conductivity
+    contrast 1e4, FP32 line solves with the FP64 residual refinement; CUDA
+    events around `steps` steps (each field is 537 MB, larger than L2), and
+    the FP64 heat balance of one step measured by the library itself:
+    E(next) - E(now) - tau Q - tau/2 (Phi(now) + Phi(next)), relative to the
+    energy change.  Accuracy against the FP64 oracle is the 1024 x 2048
+    subsample test (tests/test_gpu_parity.py)."""
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver
+    p = H.config4()
+    probe = HeatSolver(p, 1.0, precision="fp32_refined")
+    tau = H.DT_FACTOR * probe.tau_exp
+    act = active_cells(probe, p)
+    probe.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = HeatSolver(p, tau, precision="fp32_refined", stream=stream)
+        s.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        E0, Phi0, Q = s.energy()
+        s.step(1)
+        E1, Phi1, _ = s.energy()
+        launches = s.launches_per_step()
+        s.close()
+    resid = (E1 - E0) - tau * Q - 0.5 * tau * (Phi0 + Phi1)
+    return {"workload": "config4: 8192x16384, k 0.04/400 (contrast 1e4), seed 4, dt=50*tau_exp",
+            "precision": "fp32_refined", "steps": steps, "ms_per_step": ms / steps,
+            "cell_steps_per_s": act * steps / (ms * 1e-3), "active_cells": act,
+            "heat_balance_rel": abs(resid) / abs(E1 - E0), "launches_per_step": launches,
+            "accuracy": "1024x2048 subsample vs FP64 oracle: tests/test_gpu_parity.py::test_config4_subsample_against_the_oracle",
+            "l2": "inputs larger than L2"}
+
+
+def time_surrogate(n_train, epochs, n_eval=512, n_infer=4096, tol=0.01, n_check=8, batch=64):
+    """Config 5: the FNO surrogate (128 x 256 grid, width 32, 12 x 12 modes, 4
+    layers) of the field after 2000 ADI steps at a fixed dt.  Training data
+    are n_train runs of the batched FP32 solver (surr_solve, device-resident);
+    surr_train runs `epochs` passes (minibatch 64, Adam, cosine decay); the
+    error is the rise-relative max error on n_eval fresh solver runs; fields/s
+    of the plain solver, of the network alone and of the solver-checked
+    inference (n_check members re-solved, fallback to the solver for the whole
+    batch when one exceeds tol), on the same n_infer parameter sets."""
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver, Surrogate
+    from workloads import fno as F
+    D = F.FnoDims()
+    ref = H.config5_reference_problem()
+    probe = HeatSolver(ref, 1.0, precision="fp64")
+    dt = H.DT_FACTOR * probe.tau_exp
+    probe.close()
+    params = H.config5_params(n_train + n_eval + n_infer, seed=5)
+    ptr, pev, pin = params[:n_train], params[n_train:n_train + n_eval], params[n_train + n_eval:]
+    s = Surrogate(H.config5_problem(params[0]), D, heater=H.HEATER, dt=dt, steps=2000, max_batch=batch)
+    s.set_params(F.init_params(D, 7).astype(np.float32))
+    cells = D.Nz * D.Nr
+    out = {"workload": "config5: FNO 128x256, width 32, 12x12 modes, 4 layers, horizon 2000 steps, seed 5",
+           "n_train": n_train, "epochs": epochs, "n_eval": n_eval, "n_infer": n_infer, "tol": tol,
+           "n_check": n_check, "n_params": s.n_params}
+    data = torch.empty((n_train + n_eval, D.Nz, D.Nr), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    s.solve(np.concatenate([ptr, pev]), out=data)
+    torch.cuda.synchronize()
+    out["data_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out["final_loss"] = s.train(ptr, data[:n_train], epochs=epochs, batch=batch, lr=1e-3, lr_min_frac=0.02, seed=1)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    err = s.errors(pev, data[n_train:])
+    out["eval_err"] = {"p50": float(np.percentile(err, 50)), "p90": float(np.percentile(err, 90)),
+                       "p99": float(np.percentile(err, 99)), "max": float(err.max()),
+                       "frac_le_tol": float(np.mean(err <= tol))}
+    del data
+    T = torch.empty((n_infer, D.Nz, D.Nr), dtype=torch.float32, device="cuda")
+    s.forward(pin[:batch], out=T[:batch])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.solve(pin, out=T)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.forward(pin, out=T)
+    torch.cuda.synchronize()
+    t_net = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, used, cerr = s.infer_checked(pin, n_check=n_check, tol=tol, seed=3, out=T)
+    torch.cuda.synchronize()
+    t_chk = time.perf_counter() - t0
+    s.close()
+    # the plain batched solver without its per-call setup: 512 members of the
+    # same cell, 2000 graph-replayed steps
+    from paper_1912_03744_gb300 import HeatBatch
+    nb = 512
+    b = HeatBatch([H.config5_problem(x) for x in pin[:nb]], [dt] * nb, precision="fp32")
+    b.step(10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(2000)
+    b.sync()
+    t_steps = time.perf_counter() - t0
+    b.close()
+    out["fields_per_s"] = {"solver": n_infer / t_solve, "solver_steps_only": nb / t_steps,
+                           "network": n_infer / t_net, "checked": n_infer / t_chk}
+    out["checked"] = {"used_fallback": used, "max_checked_err": cerr}
+    out["gain_checked_over_solver"] = t_solve / t_chk
+    out["solver_cell_steps_per_s"] = n_infer * cells * 2000 / t_solve
+    return out
+
+
 def cpu_baseline(p, budget_s=12.0, max_steps=50):
     """The FP64 oracle as it stands, all host cores, bounded number of steps."""
     import oracle
@@ -278,6 +393,11 @@ def main():
     ap.add_argument("--ensemble-only", action="store_true", help="time the ensemble leg only; for profiling")
     ap.add_argument("--ensemble-tuning", default=None,
                     help="K,band,zwpb: fixed ensemble schedule instead of the autotuner")
+    ap.add_argument("--no-config4", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-train", type=int, default=4096, help="solver runs the surrogate trains on")
+    ap.add_argument("--surrogate-epochs", type=int, default=10)
+    ap.add_argument("--config4-steps", type=int, default=20)
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=4096)
     args = ap.parse_args()
@@ -322,6 +442,8 @@ def main():
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
     ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning)
+    c4 = None if args.no_config4 else time_config4(args.config4_steps, args.warmup)
+    surr = None if args.no_surrogate else time_surrogate(args.surrogate_train, args.surrogate_epochs)
     _barrier(ws)
 
     tot_ms = sum(main_t["r_ms"]) + sum(main_t["z_ms"])
@@ -368,6 +490,8 @@ def main():
         "gpu_launches": main_t["launches"],
         "clocks": clk.summary(),
         "ensemble": ens,
+        "config4": c4,
+        "surrogate": surr,
         "side_by_side": {other: {"value": act / (side_ms * 1e-3), "ms_per_step": side_ms,
                                  "steps": len(side_t["r_ms"]), "roofline": roof(side_t, other)}},
     }

@@ -11,22 +11,27 @@
  *
  * Network (all sizes from surr_dims; the default is 128 x 256, width 32,
  * 12 x 12 modes, 4 layers):
- *   features (9 per cell): 2 (ln k_m - ln 0.1)/(ln 400 - ln 0.1) - 1 (m < 5),
- *     2 (q - 1e5)/(1e7 - 1e5) - 1, (T_D - 300)/50, 2 r_i/R - 1, 2 z_j/Z - 1
+ *   features (16 per cell): x_m = 2 (ln k_m - ln 0.1)/(ln 400 - ln 0.1) - 1
+ *     (m < 5), x_5 = 2 (q - 1e5)/(1e7 - 1e5) - 1, x_6 = (T_D - 300)/50 (these
+ *     7 broadcast over the grid), 2 r_i/R - 1, 2 z_j/Z - 1, then per cell:
+ *     the one-hot region of the cell (5 channels; region = the first box
+ *     containing the cell centre, all 0 on void cells), x_{region} (0 on void)
+ *     and x_5 on cells of heater_region (0 elsewhere)
  *   lift v_0 = P x + pb (C channels); for l < L:
  *     pre_l = K_l(v_l) + W_l v_l + wb_l, v_{l+1} = gelu(pre_l) (l < L-1) or pre_l,
  *     K_l(v) = irfft2(pad(R_l . trunc(rfft2(v)))) over (z, r), keeping
  *     kz in {0..mz-1, Nz-mz..Nz-1}, kr in {0..mr-1}, a complex C x C matrix
  *     per kept mode;
  *   h = gelu(Q1 v_L + q1b) (2C channels), u = Q2 h + q2b (2 channels),
- *   T = T_init + 0.02 q u_0 + (T_D - T_init) u_1   (the scheme is linear in
- *     its source and its Dirichlet value);
+ *   T = T_init + m (0.02 q u_0 + (T_D - T_init) u_1)   (the scheme is linear
+ *     in its source and its Dirichlet value; m = 1 on cells of a region box,
+ *     0 on void cells, which the scheme keeps at T_init);
  *   gelu(x) = x/2 (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))).
  * Loss: mean over samples and cells of ((T - T_true)/(0.02 q))^2.
  * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
  * cores (mma.sync m16n8k16), FP32 master weights, Adam in FP32.
  *
- * Flat parameter vector (FP32), in order: P[C][9], pb[C]; per layer l:
+ * Flat parameter vector (FP32), in order: P[C][16], pb[C]; per layer l:
  * W_l[C][C], wb_l[C], Rre_l[2mz][mr][C][C], Rim_l[2mz][mr][C][C] (indexed
  * kz-index, kr, input channel, output channel); Q1[2C][C], q1b[2C],
  * Q2[2][2C], q2b[2].

@@ -12,8 +12,12 @@ map (5 region conductivities k, heater power q, Dirichlet temperature T_D)
 primitive; everything else is explicit array arithmetic.
 
 Definition:
-  features  x_f (9 channels): 5 x scaled ln k, scaled q, scaled T_D (all
-            broadcast over the grid), scaled r and z cell centres
+  features  x_f (16 channels): 5 x scaled ln k, scaled q, scaled T_D (all
+            broadcast over the grid), scaled r and z cell centres, the one-hot
+            region of the cell (5 channels, all 0 on void), the cell's own
+            scaled ln k (0 on void) and the scaled q on heater cells (0
+            elsewhere): the geometry is fixed, so these are positional
+            features that tell the network which material each cell holds
   lift      v_0 = P x + pb                                  (C channels)
   layer l   pre_l = K_l(v_l) + W_l v_l + wb_l,
             v_{l+1} = gelu(pre_l) for l < L-1, pre_l for the last layer
@@ -56,13 +60,17 @@ class FnoOracle:
     """FNO forward, loss, backward and Adam in FP64.
 
     d: a ``workloads.fno.FnoDims``; rc [Nr], zc [Nz]: cell centres; R, Z: the
-    outer radius and height used to scale the coordinates; active [Nz, Nr]:
-    the active-cell indicator m (all ones if None)."""
+    outer radius and height used to scale the coordinates; region [Nz, Nr]:
+    the region of each cell (0..4, -1 on void; all 0 if None), whose
+    indicator region >= 0 is the active-cell mask m; heater: the region that
+    holds the source q."""
 
-    def __init__(self, d, rc, zc, R, Z, T_init=300.0, active=None):
+    def __init__(self, d, rc, zc, R, Z, T_init=300.0, region=None, heater=2):
         self.d = d
-        self.m = np.ones((d.Nz, d.Nr)) if active is None else np.asarray(active, dtype=np.float64)
-        assert self.m.shape == (d.Nz, d.Nr)
+        self.region = np.zeros((d.Nz, d.Nr), dtype=np.int64) if region is None else np.asarray(region, dtype=np.int64)
+        assert self.region.shape == (d.Nz, d.Nr)
+        self.m = (self.region >= 0).astype(np.float64)
+        self.heater = int(heater)
         self.rc = np.asarray(rc, dtype=np.float64)
         self.zc = np.asarray(zc, dtype=np.float64)
         assert self.rc.shape == (d.Nr,) and self.zc.shape == (d.Nz,)
@@ -83,17 +91,22 @@ class FnoOracle:
     def pack(self, parts):
         return np.concatenate([parts[name].ravel() for name, _ in self.d.sizes()])
 
-    # ---- features: [B, 9, Nz, Nr]
+    # ---- features: [B, 16, Nz, Nr]
     def features(self, params):
         p = np.asarray(params, dtype=np.float64).reshape(-1, 7)
         B, d = p.shape[0], self.d
-        x = np.empty((B, 9, d.Nz, d.Nr))
+        x = np.zeros((B, 16, d.Nz, d.Nr))
         for m in range(5):
             x[:, m] = (2.0 * (np.log(p[:, m]) - LNK_LO) / (LNK_HI - LNK_LO) - 1.0)[:, None, None]
         x[:, 5] = (2.0 * (p[:, 5] - Q_LO) / (Q_HI - Q_LO) - 1.0)[:, None, None]
         x[:, 6] = ((p[:, 6] - TD_MID) / TD_HALF)[:, None, None]
         x[:, 7] = (2.0 * self.rc / self.R - 1.0)[None, None, :]
         x[:, 8] = (2.0 * self.zc / self.Z - 1.0)[None, :, None]
+        for m in range(5):
+            on = self.region == m
+            x[:, 9 + m] = on[None].astype(np.float64)
+            x[:, 14] += on[None] * x[:, m]
+        x[:, 15] = (self.region == self.heater)[None] * x[:, 5]
         return x
 
     # ---- spectral convolution and its adjoints

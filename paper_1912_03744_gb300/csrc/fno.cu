@@ -37,6 +37,7 @@ constexpr double kQLo = 1.0e5, kQHi = 1.0e7;
 constexpr double kTdMid = 300.0, kTdHalf = 50.0;
 constexpr double kSQ = 0.02;
 constexpr int kSplit = 16;  // split-K factor of the weight-gradient GEMMs
+constexpr int kF = 16;      // input features per cell (include/surrogate.h)
 constexpr double kPiD = 3.14159265358979323846;
 
 int cuda_status(cudaError_t e)
@@ -64,61 +65,108 @@ __device__ __forceinline__ void features(const double *__restrict__ p, float rno
     x[8] = znorm;
 }
 
-// v0[b][c][p] = P x + pb   (one thread per (b, p))
+// The 16 features of cell p of a sample whose 7 per-sample features are xs:
+// xs, r, z, the one-hot region of the cell (reg[p], -1 on void), the cell's
+// ln k feature and the heater source feature.
+__device__ __forceinline__ void cell_features(const float (&xs)[7], float r, float z, int reg, int heater,
+                                              float (&x)[kF])
+{
+#pragma unroll
+    for (int f = 0; f < 7; ++f) x[f] = xs[f];
+    x[7] = r;
+    x[8] = z;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) x[9 + m] = reg == m ? 1.f : 0.f;
+    x[14] = reg >= 0 && reg < 5 ? xs[reg] : 0.f;
+    x[15] = reg == heater ? xs[5] : 0.f;
+}
+
+// v0[b][c][p] = P x + pb.  Grid (chunks of p, B): the 7 features of sample
+// b are formed once per block (FP64 logarithms) and shared.
 __global__ void lift_kernel(const double *__restrict__ params, const float *__restrict__ rn,
-                            const float *__restrict__ zn, int B, int Nz, int Nr, int C, const float *__restrict__ Pw,
-                            const float *__restrict__ pb, bf16 *__restrict__ v0)
+                            const float *__restrict__ zn, const signed char *__restrict__ reg, int heater, int B,
+                            int Nz, int Nr, int C, const float *__restrict__ Pw, const float *__restrict__ pb,
+                            bf16 *__restrict__ v0)
 {
     const long long P = (long long)Nz * Nr;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < B * P; t += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(t / P);
-        const long long p = t - b * P;
+    const int b = blockIdx.y;
+    __shared__ float sxs[7];
+    if (threadIdx.x == 0) {
+        float x9[9];
+        features(params + 7 * b, 0.f, 0.f, x9);
+        for (int f = 0; f < 7; ++f) sxs[f] = x9[f];
+    }
+    __syncthreads();
+    float xs[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) xs[f] = sxs[f];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(p / Nr), i = (int)(p - (long long)j * Nr);
-        float x[9];
-        features(params + 7 * b, rn[i], zn[j], x);
+        float x[kF];
+        cell_features(xs, rn[i], zn[j], reg[p], heater, x);
         bf16 *dst = v0 + (long long)b * C * P + p;
         for (int c = 0; c < C; ++c) {
             float s = pb[c];
 #pragma unroll
-            for (int f = 0; f < 9; ++f) s = fmaf(Pw[c * 9 + f], x[f], s);
+            for (int f = 0; f < kF; ++f) s = fmaf(Pw[c * kF + f], x[f], s);
             dst[(long long)c * P] = __float2bfloat16(s);
         }
     }
 }
 
-// dP[c][f] += sum dv0[b][c][p] x_f,  dpb[c] += sum dv0   (block per (c, chunk))
+// dP[c][f] += sum over b, p of dv0[b][c][p] x_f,  dpb[c] += sum dv0.  Block per
+// (b, c): the row sums S = sum_p dv0, Sr = sum_p dv0 r_i, Sz = sum_p dv0 z_j and
+// S_m = sum over the cells of region m of dv0; then the 7 per-sample features
+// contribute x_f(b) S, the coordinates Sr and Sz, the one-hot channels S_m,
+// the cell ln k channel sum_m x_m(b) S_m and the heater channel x_5(b) S_heater.
 __global__ void lift_bwd_kernel(const double *__restrict__ params, const float *__restrict__ rn,
-                                const float *__restrict__ zn, int B, int Nz, int Nr, int C,
-                                const float *__restrict__ dv0, float *__restrict__ gP, float *__restrict__ gpb)
+                                const float *__restrict__ zn, const signed char *__restrict__ reg, int heater, int B,
+                                int Nz, int Nr, int C, const float *__restrict__ dv0, float *__restrict__ gP,
+                                float *__restrict__ gpb)
 {
-    const int c = blockIdx.y;
+    const int c = blockIdx.x, b = blockIdx.y;
     const long long P = (long long)Nz * Nr;
-    float acc[10];
+    const float *__restrict__ row = dv0 + ((long long)b * C + c) * P;
+    float acc[8];
 #pragma unroll
-    for (int f = 0; f < 10; ++f) acc[f] = 0.f;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < B * P; t += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(t / P);
-        const long long p = t - b * P;
+    for (int f = 0; f < 8; ++f) acc[f] = 0.f;
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
         const int j = (int)(p / Nr), i = (int)(p - (long long)j * Nr);
-        float x[9];
-        features(params + 7 * b, rn[i], zn[j], x);
-        const float g = dv0[((long long)b * C + c) * P + p];
+        const float g = row[p];
+        const int r = reg[p];
+        acc[0] += g;
+        acc[1] = fmaf(g, rn[i], acc[1]);
+        acc[2] = fmaf(g, zn[j], acc[2]);
 #pragma unroll
-        for (int f = 0; f < 9; ++f) acc[f] = fmaf(g, x[f], acc[f]);
-        acc[9] += g;
+        for (int m = 0; m < 5; ++m) acc[3 + m] += r == m ? g : 0.f;
     }
-    __shared__ float red[10][256];
+    __shared__ float red[8][256];
 #pragma unroll
-    for (int f = 0; f < 10; ++f) red[f][threadIdx.x] = acc[f];
+    for (int f = 0; f < 8; ++f) red[f][threadIdx.x] = acc[f];
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
 #pragma unroll
-            for (int f = 0; f < 10; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + s];
+            for (int f = 0; f < 8; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x < 9) atomicAdd(&gP[c * 9 + threadIdx.x], red[threadIdx.x][0]);
-    if (threadIdx.x == 9) atomicAdd(&gpb[c], red[9][0]);
+    if (threadIdx.x == 0) {
+        float x[9];
+        features(params + 7 * b, 0.f, 0.f, x);
+        const float S = red[0][0];
+        float* g = gP + (size_t)c * kF;
+        for (int f = 0; f < 7; ++f) atomicAdd(&g[f], x[f] * S);
+        atomicAdd(&g[7], red[1][0]);
+        atomicAdd(&g[8], red[2][0]);
+        float lnk = 0.f;
+        for (int m = 0; m < 5; ++m) {
+            atomicAdd(&g[9 + m], red[3 + m][0]);
+            lnk = fmaf(x[m], red[3 + m][0], lnk);
+        }
+        atomicAdd(&g[14], lnk);
+        if (heater >= 0 && heater < 5) atomicAdd(&g[15], x[5] * red[3 + heater][0]);
+        atomicAdd(&gpb[c], S);
+    }
 }
 
 // P2 [BC][2MZ][2mr] -> Xm [MZ*mr][B][2C]
@@ -205,8 +253,9 @@ __global__ void mix_in_bwd_kernel(const float *__restrict__ gXm, int B, int C, i
 // With Ttrue: loss sum += e^2 (e = (T - Ttrue)/(S_Q q)) and gu = dL/du (BF16).
 __global__ void head_kernel(const bf16 *__restrict__ h, const double *__restrict__ params, int B, long long P, int H,
                             const float *__restrict__ Q2, const float *__restrict__ q2b, double T_init,
-                            float *__restrict__ T, const float *__restrict__ Ttrue, double inv_ntot,
-                            bf16 *__restrict__ gu, double *__restrict__ loss)
+                            const signed char *__restrict__ reg, float *__restrict__ T,
+                            const float *__restrict__ Ttrue, double inv_ntot, bf16 *__restrict__ gu,
+                            double *__restrict__ loss)
 {
     double lsum = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < B * P; t += (long long)gridDim.x * blockDim.x) {
@@ -221,12 +270,13 @@ __global__ void head_kernel(const bf16 *__restrict__ h, const double *__restrict
         }
         const double q = params[7 * b + 5], Td = params[7 * b + 6];
         const double sc = kSQ * q;
-        const double Tv = T_init + sc * u0 + (Td - T_init) * u1;
+        const double act = reg[p] >= 0 ? 1.0 : 0.0;  // void cells hold T_init
+        const double Tv = T_init + act * (sc * u0 + (Td - T_init) * u1);
         T[t] = (float)Tv;
         if (Ttrue) {
             const double e = (Tv - (double)Ttrue[t]) / sc;
             lsum += e * e;
-            const double gT = 2.0 * e / sc * inv_ntot;
+            const double gT = 2.0 * e / sc * inv_ntot * act;
             gu[(long long)b * 2 * P + p] = __float2bfloat16((float)(gT * sc));
             gu[(long long)b * 2 * P + P + p] = __float2bfloat16((float)(gT * (Td - T_init)));
         }
@@ -397,6 +447,7 @@ struct surr_ctx {
     bf16 *Wb = nullptr, *Q1b = nullptr, *Q2b = nullptr, *Wblk = nullptr;  // BF16 working copies
     bf16 *Fr = nullptr, *Gr = nullptr, *Fz = nullptr;                      // DFT tables
     float *rn = nullptr, *zn = nullptr;
+    signed char *d_reg = nullptr;  // [Nz][Nr] region of each cell, -1 on void
     double *d_params = nullptr, *d_loss = nullptr;
     // workspace (max_batch samples)
     bf16 *act = nullptr;       // (L+1) x [B][C][P]
@@ -430,7 +481,7 @@ void free_surr(surr_ctx *s)
     void *bufs[] = {s->w,  s->g,  s->m,    s->v,    s->Wb,   s->Q1b,  s->Q2b, s->Wblk, s->Fr,   s->Gr,
                     s->Fz, s->rn, s->zn,   s->d_params, s->d_loss, s->act, s->pre, s->S,  s->A1,  s->A3,
                     s->P2, s->Yh, s->Xm,   s->Ym,   s->Ymb,  s->hpre, s->h,   s->Tout, s->Ttrue, s->gu,
-                    s->dp0, s->dp1, s->dv0, s->part, s->dWblk, s->d_idx, s->d_err};
+                    s->dp0, s->dp1, s->dv0, s->part, s->dWblk, s->d_idx, s->d_err, s->d_reg};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete s;
@@ -465,8 +516,8 @@ cudaError_t forward_chunk(surr_ctx *s, int B, bool train, const float *Ttrue, fl
     const long long actsz = (long long)s->max_batch * CP;
     cudaStream_t st = s->stream;
     cudaError_t e;
-    lift_kernel<<<grid_for(B * P), 256, 0, st>>>(s->d_params, s->rn, s->zn, B, Nz, Nr, C, s->w + s->oP, s->w + s->opb,
-                                                 s->act);
+    lift_kernel<<<dim3((unsigned)((P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024), B), 256, 0, st>>>(
+        s->d_params, s->rn, s->zn, s->d_reg, s->heater, B, Nz, Nr, C, s->w + s->oP, s->w + s->opb, s->act);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int l = 0; l < d.L; ++l) {
         const bf16 *vl = s->act + (train ? l : (l & 1)) * actsz;
@@ -538,7 +589,7 @@ cudaError_t forward_chunk(surr_ctx *s, int B, bool train, const float *Ttrue, fl
     g.Cb = s->h; g.ldc = P; g.sC1 = (long long)H * P;
     if ((e = fno::gemm(g, st)) != cudaSuccess) return e;
     head_kernel<<<grid_for(B * P), 256, 0, st>>>(s->h, s->d_params, B, P, H, s->w + s->oQ2, s->w + s->oq2b, s->T_init,
-                                                 T, Ttrue, 1.0 / ((double)B * P), s->gu, s->d_loss);
+                                                 s->d_reg, T, Ttrue, 1.0 / ((double)B * P), s->gu, s->d_loss);
     return cudaGetLastError();
 }
 
@@ -670,8 +721,8 @@ cudaError_t backward_chunk(surr_ctx *s, int B)
         dpre = dnext;
         dnext = t;
     }
-    lift_bwd_kernel<<<dim3(64, C), 256, 0, st>>>(s->d_params, s->rn, s->zn, B, Nz, Nr, C, s->dv0, gw + s->oP,
-                                                gw + s->opb);
+    lift_bwd_kernel<<<dim3(C, B), 256, 0, st>>>(s->d_params, s->rn, s->zn, s->d_reg, s->heater, B, Nz, Nr, C,
+                                               s->dv0, gw + s->oP, gw + s->opb);
     return cudaGetLastError();
 }
 
@@ -821,7 +872,7 @@ int surr_create(const surr_dims *dims, const heat_geometry *geom, const heat_mat
     // parameter offsets (the order of include/surrogate.h)
     const int C = d.C, H = s->H;
     size_t o = 0;
-    s->oP = o; o += (size_t)C * 9;
+    s->oP = o; o += (size_t)C * kF;
     s->opb = o; o += C;
     for (int l = 0; l < d.L; ++l) {
         s->oW.push_back(o); o += (size_t)C * C;
@@ -851,6 +902,7 @@ int surr_create(const surr_dims *dims, const heat_geometry *geom, const heat_mat
     A(dalloc(s->Gr, (size_t)s->W2 * d.Nr));
     A(dalloc(s->Fz, (size_t)s->Z2 * d.Nz));
     A(dalloc(s->rn, d.Nr));
+    A(dalloc(s->d_reg, (size_t)d.Nz * d.Nr));
     A(dalloc(s->zn, d.Nz));
     A(dalloc(s->d_params, B * 7));
     A(dalloc(s->d_loss, 1));
@@ -912,6 +964,20 @@ int surr_create(const surr_dims *dims, const heat_geometry *geom, const heat_mat
         A(cudaMemcpyAsync(s->Gr, gr.data(), gr.size() * sizeof(bf16), cudaMemcpyHostToDevice, s->stream));
         A(cudaMemcpyAsync(s->Fz, fz.data(), fz.size() * sizeof(bf16), cudaMemcpyHostToDevice, s->stream));
         A(cudaMemcpyAsync(s->rn, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+        // region of each cell: the first box that contains its centre (the
+        // solver's rule), -1 on void
+        std::vector<signed char> reg((size_t)Nz_ * Nr_, (signed char)-1);
+        for (int j = 0; j < Nz_; ++j)
+            for (int i = 0; i < Nr_; ++i)
+                for (size_t b = 0; b < s->boxes.size(); ++b) {
+                    const heat_box &bx = s->boxes[b];
+                    if (rc[i] >= bx.r0 && rc[i] <= bx.r1 && zc[j] >= bx.z0 && zc[j] <= bx.z1) {
+                        const int r = bx.region;
+                        reg[(size_t)j * Nr_ + i] = (signed char)(r >= 0 && r < s->n_regions ? r : -1);
+                        break;
+                    }
+                }
+        A(cudaMemcpyAsync(s->d_reg, reg.data(), reg.size(), cudaMemcpyHostToDevice, s->stream));
         A(cudaMemcpyAsync(s->zn, zn.data(), zn.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
         A(cudaMemsetAsync(s->w, 0, o * sizeof(float), s->stream));
         A(cudaMemsetAsync(s->m, 0, o * sizeof(float), s->stream));

@@ -20,8 +20,10 @@ def _oracle(d, seed=0, masked=False):
     rng = np.random.default_rng(seed)
     rc = np.sort(rng.uniform(0.1, 4.0, d.Nr))
     zc = np.sort(rng.uniform(0.1, 10.0, d.Nz))
-    act = (rng.uniform(size=(d.Nz, d.Nr)) > 0.3).astype(float) if masked else None
-    return FnoOracle(d, rc, zc, 4.2, 10.2, active=act)
+    reg = rng.integers(0, 5, size=(d.Nz, d.Nr))
+    if masked:
+        reg[rng.uniform(size=(d.Nz, d.Nr)) < 0.3] = -1
+    return FnoOracle(d, rc, zc, 4.2, 10.2, region=reg)
 
 
 def _params(n, seed):
@@ -99,6 +101,21 @@ def test_zero_spectral_weights_reduce_to_a_pointwise_mlp():
         u = w["Q2"] @ gelu(w["Q1"] @ h + w["q1b"]) + w["q2b"]
         ref = 300.0 + S_Q * p[b, 5] * u[0] + (p[b, 6] - 300.0) * u[1]
         assert abs(T[b, j, i] - ref) <= 1e-9 * abs(ref)
+
+
+def test_cell_features_follow_the_region_map():
+    d = F.SMALL
+    o = _oracle(d, seed=15, masked=True)
+    p = _params(2, 16)
+    x = o.features(p)
+    for b, j, i in [(0, 0, 0), (1, 3, 5), (0, 9, 2), (1, 15, 7)]:
+        r = o.region[j, i]
+        onehot = [1.0 if r == m else 0.0 for m in range(5)]
+        assert list(x[b, 9:14, j, i]) == onehot
+        lnk = 2.0 * (np.log(p[b, r]) - np.log(0.1)) / (np.log(400.0) - np.log(0.1)) - 1.0 if r >= 0 else 0.0
+        assert abs(x[b, 14, j, i] - lnk) <= 1e-12
+        qn = 2.0 * (p[b, 5] - 1e5) / (1e7 - 1e5) - 1.0 if r == 2 else 0.0
+        assert abs(x[b, 15, j, i] - qn) <= 1e-12
 
 
 def test_void_cells_hold_the_initial_temperature():

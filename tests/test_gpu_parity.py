@@ -233,3 +233,29 @@ def test_refined_path_reduces_the_solve_error_at_high_contrast():
         s.step(50)
         assert _rel(s.field(), o2.field()) <= 1e-5
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_refined"])
+def test_config4_subsample_against_the_oracle(precision):
+    """Config 4 as its accuracy is specified: the 1e4 conductivity contrast
+    (0.04 against 400) on the 1024 x 2048 subsample grid, 200 steps, against
+    the FP64 oracle.  Bars: relative max-norm 1e-5 over the field; the FP64
+    energy change E(T) - E(T_init) within 1e-5 of the oracle's."""
+    p = H.config4(1024, 2048)
+    o = Oracle(p)
+    tau = H.DT_FACTOR * o.tau_exp()
+    E_init = o.energy()[0]
+    o.step(tau, 200)
+    To = o.field()
+    Eo = o.energy()[0]
+    s = _solver(p, tau, precision)
+    s.step(200)
+    Tg = s.field()
+    E, _, _ = s.energy()
+    s.close()
+    rel = _rel(Tg, To)
+    rise = float(np.max(np.abs(Tg - To)) / np.max(np.abs(To - p.T_init)))
+    derr = abs((E - E_init) - (Eo - E_init)) / abs(Eo - E_init)
+    print(f"config4 1024x2048 {precision}: rel max {rel:.3e}, rise-relative {rise:.3e}, energy change {derr:.3e}")
+    assert rel <= 1e-5, rel
+    assert derr <= 1e-5, derr

@@ -43,7 +43,8 @@ def _setup(max_batch=8):
     dt = H.DT_FACTOR * Oracle(ref).tau_exp()
     s = Surrogate(p0, D, heater=H.HEATER, dt=dt, steps=STEPS, max_batch=max_batch)
     g = Oracle(p0).grid()
-    fo = FnoOracle(D, g["rc"], g["zc"], p0.r_faces[-1], p0.z_faces[-1], T_init=p0.T_init)
+    fo = FnoOracle(D, g["rc"], g["zc"], p0.r_faces[-1], p0.z_faces[-1], T_init=p0.T_init, region=g["region"],
+                   heater=H.HEATER)
     return s, fo, params, dt
 
 
@@ -130,4 +131,47 @@ def test_fallback_returns_the_solver_fields_when_the_check_fails():
     T, used, err = s.infer_checked(params[:5], n_check=2, tol=0.01, seed=3)
     assert used and err > 0.01
     np.testing.assert_array_equal(T, s.solve(params[:5]))
+    s.close()
+
+
+def test_trained_network_gains_speed_over_the_solver_at_its_accuracy():
+    """What the trained network gains over the method alone.  Trained on
+    solver runs, its held-out rise-relative max error falls well below the
+    untrained network's; at a tolerance its held-out errors meet, the checked
+    inference (network + sampled solver check) returns the network's fields
+    faster than the solver alone on the same batch; at a tolerance they do not
+    meet, the check sends the batch to the solver."""
+    import time
+
+    import torch
+    s, _, _, _ = _setup(max_batch=64)
+    s.set_params(F.init_params(D, 40).astype(np.float32))
+    n_tr, n_te = 2048, 256
+    params = H.config5_params(n_tr + n_te, seed=41)
+    fields = torch.empty((n_tr + n_te, D.Nz, D.Nr), dtype=torch.float32, device="cuda")
+    s.solve(params, out=fields)
+    tr, te = params[:n_tr], params[n_tr:]
+    e0 = s.errors(te, fields[n_tr:])
+    s.train(tr, fields[:n_tr], epochs=40, batch=64, lr=2e-3, seed=1)
+    e1 = s.errors(te, fields[n_tr:])
+    print(f"held-out error untrained p50 {np.median(e0):.3f}, trained p50 {np.median(e1):.3f} max {e1.max():.3f}")
+    assert np.median(e1) <= 0.3 * np.median(e0)
+    tol = 1.5 * float(e1.max())
+    out = torch.empty((n_te, D.Nz, D.Nr), dtype=torch.float32, device="cuda")
+    s.infer_checked(te[:8], n_check=2, tol=tol, out=out[:8])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.solve(te, out=out)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, used, err = s.infer_checked(te, n_check=4, tol=tol, seed=5, out=out)
+    torch.cuda.synchronize()
+    t_chk = time.perf_counter() - t0
+    print(f"fields/s solver {n_te / t_solve:.0f}, checked network {n_te / t_chk:.0f}")
+    assert not used and err <= tol
+    assert t_chk < t_solve
+    T, used, err = s.infer_checked(te[:8], n_check=4, tol=0.5 * float(e1.min()), seed=6)
+    assert used and err > 0.5 * float(e1.min())
+    np.testing.assert_array_equal(T, s.solve(te[:8]))
     s.close()

@@ -13,7 +13,8 @@ Flat parameter vector (FP32 on the device, FP64 in the oracle), in order:
         Rre_l, Rim_l [MZ, MR, C, C]  spectral weights, (kz index, kr, in c, out o)
     Q1 [H, C], q1b [H]   projection hidden layer
     Q2 [2, H], q2b [2]   projection output layer
-with F = 9 input features, H = 2 C hidden projection channels,
+with F = 16 input features (7 per-sample scalars, r, z, the cell's one-hot
+region, ln k and heater source), H = 2 C hidden projection channels,
 MZ = 2 mz kept z-modes (kz = 0..mz-1 and Nz-mz..Nz-1), MR = mr kept r-modes.
 """
 from __future__ import annotations
@@ -22,7 +23,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-N_FEATURES = 9
+N_FEATURES = 16
 
 
 @dataclass(frozen=True)
