@@ -40,10 +40,11 @@ METRIC = "cell-steps/s vs HBM roofline"
 UNIT = "cell-steps/s"
 WORKLOAD = "config2: five-region layered cell 2048x4096, seed 2, dt=50*tau_exp"
 ELEM = {"fp64": 8, "fp32": 4}
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of this workload (profiles/adi_step_config2_2048x4096_fp32.md);
-# None where no capture matches the current kernel.
-TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.952512e6 + 2.080000e6}
+# DRAM bytes (read + write) per launch of the dominant sweep from one ncu
+# capture of this workload (profiles/adi_step_config2_2048x4096_fp32.md):
+# the z-sweep is zsum2 + zcarry2 + zsolve2; None where no capture matches
+# the current kernels.
+TRAFFIC = {("zsweep", "fp32", 2048, 4096): (34.204416e6 + 0.0) + (2.128640e6 + 0.0) + (36.322304e6 + 0.763392e6)}
 
 
 def _peaks():
