@@ -175,8 +175,10 @@ struct DevTab {
 // X_c = G0_c + GP_c D_{c-1} + H_c X_{c+1} (X_n = 0): chunk c starts its
 // forward recurrence from D_{c-1} and its backward one from X_{c+1}.
 // Packed per (class, row) tables, 8 values: pkA = {inv, f, cp, e0},
-// pkB = {e1, e2, wB, wG} with (e0, e1, e2) = (q, xm, xp) for the increment
-// form, (s, w, 0) for the literal form.  Per (class, chunk): {F, H, GP, 0}.
+// pkB = {e1, e2, s6, wG} with (e0, e1, e2) = (q, xm, xp) for the increment
+// form, (s, w, 0) for the literal form, and s6 = wB on the refined path or
+// P_j = prod_{m=r0}^{j} f_m (the chunk's prefix product) on the literal and
+// increment paths.  Per (class, chunk): {F, H, GP, 0}.
 struct ZPart {
     int Rc = 0, n_chunks = 0;
     double *pk64 = nullptr, *ch64 = nullptr;  // device

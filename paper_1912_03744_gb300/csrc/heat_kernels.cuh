@@ -1486,11 +1486,13 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     int wpb = tu.zwpb;
     if (wpb != 1 && wpb != 2) wpb = (size_t)maxRc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
     tu.zwpb = wpb;
+    // the lean solve keeps no forward results: 4 warps per block, staged (P, cp) rows only
+    const int cw = lean ? 4 : wpb;
     c.fn = lean ? (const void *)zsolve2_kernel<real, V, lean ? MODE : MODE_DELTA>
                 : (const void *)zsolve_kernel<real, V, MODE>;
-    c.grid = dim3((groups + wpb - 1) / wpb, maxNch, n);
-    c.block = dim3(32 * wpb, 1, 1);
-    c.smem = (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
+    c.grid = dim3((groups + cw - 1) / cw, maxNch, n);
+    c.block = dim3(32 * cw, 1, 1);
+    c.smem = lean ? (size_t)cw * maxRc * 2 * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
     c.flip = true;
     if ((e = allow_smem(c.fn, c.smem)) != cudaSuccess) return e;
     out.push_back(a);

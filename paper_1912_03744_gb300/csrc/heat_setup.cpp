@@ -240,7 +240,7 @@ void build_tables(heat_ctx *ctx)
 // Packed z-sweep tables, chunk and run constants for the column partition
 // (see ZPart in heat_internal.h); FP64 on the host.
 static void segment_weights(const HostTab &Z, size_t o, int r0, int r1, double *wB, double *wG, double *Cout,
-                            double *F, double *H, double *GP)
+                            double *F, double *H, double *GP, double *Pout = nullptr)
 {
     const int n = r1 - r0;
     std::vector<double> C(n + 1), P(n), S(n + 1);
@@ -266,6 +266,8 @@ static void segment_weights(const HostTab &Z, size_t o, int r0, int r1, double *
     for (int k = 0; k < n; ++k) gp += P[k] * C[k];
     if (Cout)
         for (int k = 0; k < n; ++k) Cout[k] = C[k];
+    if (Pout)
+        for (int k = 0; k < n; ++k) Pout[k] = P[k];
     *F = P[n - 1];
     *H = C[n];
     if (GP) *GP = gp;
@@ -282,16 +284,20 @@ void build_zpartition(heat_ctx *ctx)
     ctx->zpk.assign((size_t)nb * Nz * 8, 0.0);
     ctx->zch.assign((size_t)nb * nch * 4, 0.0);
     const bool lit = ctx->precision == HEAT_FP64;
-    std::vector<double> wB(Rc), wG(Rc);
+    // the refined path's summary pass weights its rows by wB; the literal and
+    // increment paths take B from the zero-carry recurrence itself and need
+    // the prefix products P_j = prod f from the chunk's first row instead
+    const bool prefix = ctx->precision != HEAT_FP32_REFINED;
+    std::vector<double> wB(Rc), wG(Rc), Pp(Rc);
     for (int b = 0; b < nb; ++b) {
         const size_t o = (size_t)b * Nz;
         for (int c = 0; c < nch; ++c) {
             const int r0 = c * Rc, r1 = std::min(Nz, r0 + Rc);
             double *ch = &ctx->zch[((size_t)b * nch + c) * 4];
-            segment_weights(Z, o, r0, r1, wB.data(), wG.data(), nullptr, &ch[0], &ch[1], &ch[2]);
+            segment_weights(Z, o, r0, r1, wB.data(), wG.data(), nullptr, &ch[0], &ch[1], &ch[2], Pp.data());
             for (int k = 0; k < r1 - r0; ++k) {
                 double *e = &ctx->zpk[(o + r0 + k) * 8];
-                e[6] = wB[k];
+                e[6] = prefix ? Pp[k] : wB[k];
                 e[7] = wG[k];
             }
         }

@@ -7,11 +7,12 @@
 // the warp is one contiguous run) and one chunk of Rc rows, and every lane
 // walks its chunk row by row (interleaved Thomas).  The column partition and
 // its carry algebra are those of ZPart (heat_internal.h):
-//   zsum   : each (column, chunk) to its two carry summaries B = sum r wB and
-//            G0 = sum r wG (r = right-hand side of the row);
+//   zsum   : each (column, chunk) walked forward from a zero carry; the
+//            results go to the output buffer, the carry summaries B (the
+//            last of them) and G0 = sum r wG (r = right-hand side) to scratch;
 //   zcarry : the carry recurrences of every column over its chunks;
-//   zsolve : each chunk walked forward from its carry-in (results kept in
-//            shared memory) and back from its other carry, new field stored.
+//   zsolve : each chunk walked back from its carries, correcting every
+//            forward result by the carry-in times a prefix product of f.
 // Rows are fetched ZP at a time and double-buffered: the loads of the next
 // ZP rows (and of the warp's left / right halo columns) are in flight while
 // the current ZP rows are computed.  Table rows of the lane's column class
@@ -282,10 +283,14 @@ struct ZWalk {
     }
 };
 
-// Pass 1: summaries B = sum r wB and G0 = sum r wG of every (column, chunk):
-// zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks, instances).
+// Pass 1: every (column, chunk) walked forward from a zero carry.  The
+// results d0_j (the forward recurrence with a zero carry-in) are stored in the
+// output field buffer -- during the z-sweep it holds the superseded field --
+// and the chunk's carry summaries B = d0 at its last row and G0 = sum r wG go
+// to zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks,
+// instances).
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
+__global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
     const SweepArgs<real> &A = args[blockIdx.z];
@@ -296,17 +301,28 @@ __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__res
     if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    real *__restrict__ d0out = flip ? A.f0 : A.f1;
     ZWalk<real, V, MODE> W;
     W.init(A, flip ? A.f1 : A.f0, grp * 32 * V + lane * V, lane, j0, j1);
-    real sb[V], sg[V];
+    real dl[V], sg[V];
 #pragma unroll
-    for (int q = 0; q < V; ++q) sb[q] = sg[q] = real(0);
-    auto emit = [&](int, const real(&d)[V], const auto &e) {
+    for (int q = 0; q < V; ++q) dl[q] = sg[q] = real(0);
+    auto emit = [&](int j, const real(&d)[V], const auto &e) {
         constexpr int E = sizeof(e) / sizeof(e[0]);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            sb[q] = fmad(d[q], e[E == 1 ? 0 : q][6], sb[q]);
+            dl[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dl[q]);
             sg[q] = fmad(d[q], e[E == 1 ? 0 : q][7], sg[q]);
+        }
+        if (W.any) {
+            real *row = d0out + (size_t)j * Nr + W.ib;
+            if (W.vec) {
+                ZVec<real, V>::st(row, dl);
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    if (W.ib + q < Nr) row[q] = dl[q];
+            }
         }
     };
     extern __shared__ __align__(16) unsigned char zs_smem[];
@@ -321,128 +337,139 @@ __global__ void __launch_bounds__(128) zsum2_kernel(const SweepArgs<real> *__res
     real *__restrict__ zs = A.zs;
     if (W.vec) {
         if (W.any) {
-            ZVec<real, V>::st(zs + ((size_t)c * 2) * Nr + W.ib, sb);
+            ZVec<real, V>::st(zs + ((size_t)c * 2) * Nr + W.ib, dl);
             ZVec<real, V>::st(zs + ((size_t)c * 2 + 1) * Nr + W.ib, sg);
         }
     } else {
 #pragma unroll
         for (int q = 0; q < V; ++q)
             if (W.ib + q < Nr) {
-                zs[((size_t)c * 2) * Nr + W.ib + q] = sb[q];
+                zs[((size_t)c * 2) * Nr + W.ib + q] = dl[q];
                 zs[((size_t)c * 2 + 1) * Nr + W.ib + q] = sg[q];
             }
     }
 }
 
-// Pass 3: solve every (column, chunk) from its carries.  Shared memory holds
-// each warp's forward results, [warps][Rc][32 V] reals.
+// Pass 3: every (column, chunk) walked back from its carries: with
+// D = the forward carry into the chunk and X = the backward carry from above,
+//   d'_j = d0_j + P_j D   (P_j = prod f from the chunk's first row to j),
+//   x_j  = d'_j + cp_j x_{j+1},
+// and the new field is theta + x (increment form) or x (literal form).  Rows
+// of d0 and theta are fetched ZQ at a time, double-buffered.
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(64) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
+__global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
     const SweepArgs<real> &A = args[blockIdx.z];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
-    real *__restrict__ out = flip ? A.f0 : A.f1;
+    real *__restrict__ out = flip ? A.f0 : A.f1;  // holds d0 on entry
     const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     if ((int)blockIdx.y >= A.nch) return;
     constexpr int COLS = 32 * V;
+    constexpr bool LIT = MODE == MODE_LIT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int grp = blockIdx.x * (blockDim.x >> 5) + w;
     if (grp * COLS >= Nr) return;  // whole warp past the field (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    const int ib = grp * COLS + lane * V;
+    const bool any = ib < Nr, vec = (Nr % V) == 0;
+    const real *__restrict__ pkA = A.pkA;
+    const real *__restrict__ pkB = A.pkB;
+    int b[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) b[q] = ib + q < Nr ? A.colcls[ib + q] : (any ? A.colcls[ib] : 0);
+    bool uni = true;
+#pragma unroll
+    for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
+    const int bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
+    const bool wuni = __all_sync(HEAT_FULL_MASK, !any || (uni && b[0] == bw));
+    // staged (P_j, cp_j) of the chunk's rows for a warp of one column class
     extern __shared__ __align__(16) unsigned char zl_smem[];
-    // per warp: forward results [Rc][COLS], then the staged table rows [Rc][8]
-    real *wsm = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * (COLS + 8);
-    real *dsm = wsm + lane * V;
-    ZWalk<real, V, MODE> W;
-    W.init(A, th, grp * COLS + lane * V, lane, j0, j1);
-    const bool wuni = W.warp_uniform();
-    if (wuni) W.stage(wsm + (size_t)Rc * COLS);
+    real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * 2;
+    if (wuni) {
+        for (int r = lane; r < j1 - j0; r += 32) {
+            const size_t o = (size_t)bw * Nz + j0 + r;
+            stg[2 * r] = __ldg(pkB + 4 * o + 2);
+            stg[2 * r + 1] = __ldg(pkA + 4 * o + 2);
+        }
+        __syncwarp();
+    }
     pdl_wait();
     const real *__restrict__ zc = A.zc;
-    real dp[V], x[V];
+    real D[V], x[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-        const bool in = W.ib + q < Nr;
-        dp[q] = in ? zc[((size_t)c * 2) * Nr + W.ib + q] : real(0);
-        x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + W.ib + q] : real(0);
+        const bool in = ib + q < Nr;
+        D[q] = in ? zc[((size_t)c * 2) * Nr + ib + q] : real(0);
+        x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + ib + q] : real(0);
     }
-    auto emit = [&](int j, const real(&d)[V], const auto &e) {
-        constexpr int E = sizeof(e) / sizeof(e[0]);
+    auto ldrow = [&](const real *__restrict__ src, int j, real (&v)[V]) {
+        const real *p = src + (size_t)j * Nr + ib;
+        if (vec && any) {
+            ZVec<real, V>::ld(p, v);
+        } else {
 #pragma unroll
-        for (int q = 0; q < V; ++q) dp[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dp[q]);
-        ZVec<real, V>::st(dsm + (size_t)(j - j0) * COLS, dp);
+            for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : real(0);
+        }
     };
-    if (wuni) W.template walk<1>(A.ucls[c], A.R, emit);
-    else W.template walk<V>(A.ucls[c], A.R, emit);
-    // backward from the carry-out; the rows the increments are added to and
-    // the cp values are fetched ZQ rows ahead
-    const real *__restrict__ pkA = A.pkA;
-    auto fetchb = [&](int x0, real (&base)[ZQ][V], real (&cpv)[ZQ][V]) {
+    auto fetch = [&](int x0, real (&dz)[ZQ][V], real (&bs)[ZQ][V]) {
 #pragma unroll
         for (int p = 0; p < ZQ; ++p) {
             const int j = x0 - p;
             if (j >= j0) {
-                if constexpr (MODE != MODE_LIT) W.row(th, j, base[p]);
-                if (wuni) {
-                    const real cv = W.stg[(size_t)(j - j0) * 8 + 2];
-#pragma unroll
-                    for (int q = 0; q < V; ++q) cpv[p][q] = cv;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < V; ++q) cpv[p][q] = __ldg(pkA + 4 * ((size_t)W.b[q] * Nz + j) + 2);
-                }
+                ldrow(out, j, dz[p]);
+                if constexpr (!LIT) ldrow(th, j, bs[p]);
             }
         }
     };
-    auto procb = [&](int x0, const real (&base)[ZQ][V], const real (&cpv)[ZQ][V]) {
+    auto proc = [&](int x0, const real (&dz)[ZQ][V], const real (&bs)[ZQ][V]) {
 #pragma unroll
         for (int p = 0; p < ZQ; ++p) {
             const int j = x0 - p;
             if (j >= j0) {
-                real dd[V];
-                {
-                    const real *ps = dsm + (size_t)(j - j0) * COLS;
-                    if constexpr (sizeof(real) == 4) {
-                        const float4 a = *reinterpret_cast<const float4 *>(ps);
-                        dd[0] = a.x, dd[1] = a.y, dd[2] = a.z, dd[3] = a.w;
-                    } else {
-                        const double2 a = *reinterpret_cast<const double2 *>(ps);
-                        dd[0] = a.x, dd[1] = a.y;
+                real Pj[V], cpj[V];
+                if (wuni) {
+                    const real pv = stg[2 * (j - j0)], cv = stg[2 * (j - j0) + 1];
+#pragma unroll
+                    for (int q = 0; q < V; ++q) Pj[q] = pv, cpj[q] = cv;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        const size_t o = (size_t)b[q] * Nz + j;
+                        Pj[q] = __ldg(pkB + 4 * o + 2);
+                        cpj[q] = __ldg(pkA + 4 * o + 2);
                     }
                 }
                 real o[V];
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
-                    x[q] = fmad(cpv[p][q], x[q], dd[q]);
-                    o[q] = MODE == MODE_LIT ? x[q] : base[p][q] + x[q];
+                    x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
+                    o[q] = LIT ? x[q] : bs[p][q] + x[q];
                 }
-                if (W.any) {
-                    real *orow = out + (size_t)j * Nr + W.ib;
-                    if (W.vec) {
+                if (any) {
+                    real *orow = out + (size_t)j * Nr + ib;
+                    if (vec) {
                         ZVec<real, V>::st(orow, o);
                     } else {
 #pragma unroll
                         for (int q = 0; q < V; ++q)
-                            if (W.ib + q < Nr) orow[q] = o[q];
+                            if (ib + q < Nr) orow[q] = o[q];
                     }
                 }
             }
         }
     };
-    {
-        real ba[ZQ][V], ca[ZQ][V], bb[ZQ][V], cb[ZQ][V];
-        fetchb(j1 - 1, ba, ca);
+    real da[ZQ][V], ba[ZQ][V], db[ZQ][V], bb[ZQ][V];
+    fetch(j1 - 1, da, ba);
 #pragma unroll 1
-        for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
-            const bool h1 = x0 - ZQ >= j0;
-            if (h1) fetchb(x0 - ZQ, bb, cb);
-            procb(x0, ba, ca);
-            if (h1) {
-                if (x0 - 2 * ZQ >= j0) fetchb(x0 - 2 * ZQ, ba, ca);
-                procb(x0 - ZQ, bb, cb);
-            }
+    for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
+        const bool h1 = x0 - ZQ >= j0;
+        if (h1) fetch(x0 - ZQ, db, bb);
+        proc(x0, da, ba);
+        if (h1) {
+            if (x0 - 2 * ZQ >= j0) fetch(x0 - 2 * ZQ, da, ba);
+            proc(x0 - ZQ, db, bb);
         }
     }
 }
