@@ -5,9 +5,11 @@
 // A block holds 256 / G line slots (or one line of G <= 256 threads); slot s
 // walks a band of consecutive rows.  The line matrix is fixed per row class,
 // so each thread keeps its K cells' coefficients {xm, xp, q, inv} in
-// registers for as long as the rows it walks keep their class; f = xm inv and
-// cp = xp inv are the Thomas multipliers (at the line ends they multiply a
-// zero carry, so the folded Dirichlet couplings there do no harm).
+// registers for as long as the rows it walks keep their class, pre-scaled by
+// the pivot: xm inv (= the Thomas multiplier f), xp inv (= cp), q inv, inv
+// (at the line ends f and cp multiply a zero carry, so the folded Dirichlet
+// couplings there do no harm); the right-hand side is formed times inv, so
+// each recurrence step is one FMA.
 // A pass solves n = 2 rows of one class (1 at a class change):
 //   right-hand side of every cell (rows j-1, j, j+1, j+2 from the ring);
 //   forward: chunk summary B (recurrence from a zero carry), team scan of
@@ -109,20 +111,38 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     };
     // column class of the thread's cells: one for all K, or per cell (a chunk
     // across a layer interface)
+    // zc0: class of the first cell, zc1: of the last cell inside the field;
+    // bit k of zsel set for cells of class zc1 (!= zc0); zmany when a cell has
+    // a third class (a layer thinner than K cells), whose cells are redone
     const int zc0 = i0 < Nr ? colcls[i0] : 0;
-    bool zuni = true;
+    int zc1 = zc0;
 #pragma unroll
-    for (int k = 1; k < K; ++k) zuni = zuni && (i0 + k >= Nr || colcls[i0 + k] == zc0);
+    for (int k = 1; k < K; ++k)
+        if (i0 + k < Nr) zc1 = colcls[i0 + k];
+    unsigned zsel = 0;
+    bool zmany = false;
+#pragma unroll
+    for (int k = 1; k < K; ++k)
+        if (i0 + k < Nr) {
+            const int c = colcls[i0 + k];
+            if (c == zc1 && c != zc0) zsel |= 1u << k;
+            zmany = zmany || (c != zc0 && c != zc1);
+        }
 
     pdl_wait();
     // prologue: rows jstart-1 .. jstart+NRING-2
     for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
 
-    // class state
+    // class state: the coefficients scaled by the pivot, fx = xm inv (also
+    // the Thomas multiplier f), cx = xp inv (also cp), qi = q inv, and inv
     int acls = -1;
-    real xm[K], xp[K], qv[K], iv[K];
+    real fx[K], cx[K], qi[K], iv[K];
     real Fc = real(1), Hc = real(1);  // products of f and cp over the chunk
     real m[5], Fe = real(1), n[5], He = real(1);
+    // wide lines: lane v's multiplier of warp v's forward map into this
+    // warp's carry, prod of F over the warps between (0 for v >= wil), and
+    // of warp v's backward map, prod of H over the warps between (0 for v <= wil)
+    real jf = real(0), jh = real(0);
 
     // load the coefficients of class a and the scan multipliers (all threads of the slot)
     auto load_class = [&](int a) {
@@ -131,16 +151,16 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         for (int k = 0; k < K; ++k) {
             const int i = i0 + k;
             const bool in = i < Nr;
-            xm[k] = in ? R.xm[ro + i] : real(0);
-            xp[k] = in ? R.xp[ro + i] : real(0);
-            qv[k] = in ? R.q[ro + i] : real(0);
             iv[k] = in ? R.inv[ro + i] : real(0);
+            fx[k] = in ? R.xm[ro + i] * iv[k] : real(0);
+            cx[k] = in ? R.xp[ro + i] * iv[k] : real(0);
+            qi[k] = in ? R.q[ro + i] * iv[k] : real(0);
         }
         Fc = Hc = real(1);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            Fc *= xm[k] * iv[k];
-            Hc *= xp[k] * iv[k];
+            Fc *= fx[k];
+            Hc *= cx[k];
         }
         // level multipliers of the team scans: m_l = prod F over lanes ls-2^l+1..ls
         // (0 below 2^l), n_l = prod H over lanes ls..ls+2^l-1 (0 past the team)
@@ -167,6 +187,26 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             if (lane == 0) sxH[slot][wil] = ph;
         }
         acls = a;
+    };
+    // (wide lines, after the barrier that publishes sxF / sxH)
+    auto join_multipliers = [&]() {
+        jf = jh = real(0);
+        if (lane < wil) {
+            jf = real(1);
+            for (int u = lane + 1; u < wil; ++u) jf *= sxF[slot][u];
+        }
+        if (lane > wil && lane < nwl) {
+            jh = real(1);
+            for (int u = wil + 1; u < lane; ++u) jh *= sxH[slot][u];
+        }
+    };
+    // sum over the first 8 lanes (the warps of a wide line are at most 8),
+    // returned to every lane of the warp
+    auto sum8 = [&](real v) {
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        return __shfl_sync(FULL, v, 0);
     };
 
     // one pass over rows j .. j+NR-1 (same class); wait first for their rows
@@ -204,32 +244,35 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             real nrt = __shfl_down_sync(FULL, xr[0], 1, W);
             if (ls == 0) nl = (i0 > 0 && i0 - 1 < Nr) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
             if (ls == W - 1) nrt = (i0 + K < Nr) ? th[(size_t)jr * Nr + i0 + K] : bc1;
-            const size_t zo = (size_t)zc0 * Nz + jr;
-            const real zm = Z.xm[zo], zp = Z.xp[zo];
+            const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
+            const real zmA = Z.xm[zo], zpA = Z.xp[zo], zmB = Z.xm[zo1], zpB = Z.xp[zo1];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
+                // the right-hand side times the pivot inv
                 const real xc = xr[k];
                 const real l = k > 0 ? xr[k - 1] : nl;
                 const real rr = k < K - 1 ? xr[k + 1] : nrt;
-                real v = fmad(xm[k], l - xc, qv[k]);
-                v = fmad(xp[k], rr - xc, v);
-                v = fmad(zm, x[r][k] - xc, v);
-                d[r][k] = fmad(zp, x[r + 2][k] - xc, v);
+                real v = fmad(fx[k], l - xc, qi[k]);
+                v = fmad(cx[k], rr - xc, v);
+                const bool bsel = (zsel >> k) & 1u;
+                const real zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
+                const real zz = fmad(zp, x[r + 2][k] - xc, zm * (x[r][k] - xc));
+                d[r][k] = fmad(iv[k], zz, v);
             }
-            if (!zuni) {
+            if (zmany) {
                 // the chunk crosses a column-class boundary: per-cell z coefficients
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const int i = i0 + k;
-                    if (i < Nr && colcls[i] != zc0) {
+                    if (i < Nr && colcls[i] != zc0 && colcls[i] != zc1) {
                         const size_t zk = (size_t)colcls[i] * Nz + jr;
                         const real xc = xr[k];
                         const real l = k > 0 ? xr[k - 1] : nl;
                         const real rr = k < K - 1 ? xr[k + 1] : nrt;
-                        real v = fmad(xm[k], l - xc, qv[k]);
-                        v = fmad(xp[k], rr - xc, v);
-                        v = fmad(Z.xm[zk], x[r][k] - xc, v);
-                        d[r][k] = fmad(Z.xp[zk], x[r + 2][k] - xc, v);
+                        real v = fmad(fx[k], l - xc, qi[k]);
+                        v = fmad(cx[k], rr - xc, v);
+                        const real zz = fmad(Z.xp[zk], x[r + 2][k] - xc, Z.xm[zk] * (x[r][k] - xc));
+                        d[r][k] = fmad(iv[k], zz, v);
                     }
                 }
             }
@@ -240,7 +283,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         for (int r = 0; r < NR; ++r) {
             real b = real(0);
 #pragma unroll
-            for (int k = 0; k < K; ++k) b = fmad(d[r][k], iv[k], (xm[k] * iv[k]) * b);
+            for (int k = 0; k < K; ++k) b = fmad(fx[k], b, d[r][k]);
             B[r] = b;
         }
 #pragma unroll
@@ -264,8 +307,8 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             rb_bar(bar_id, G);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                real D = real(0);
-                for (int v = 0; v < wil; ++v) D = fmad(sxF[slot][v], D, sxB[r][slot][v]);
+                // only lanes v < wil read a published slot (the others may hold garbage)
+                const real D = sum8(lane < wil ? jf * sxB[r][slot][lane] : real(0));
                 Din[r] = fmad(Fe, D, Din[r]);
             }
         }
@@ -274,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             real y = Din[r];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                y = fmad(d[r][k], iv[k], (xm[k] * iv[k]) * y);
+                y = fmad(fx[k], y, d[r][k]);
                 d[r][k] = y;
             }
         }
@@ -284,7 +327,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         for (int r = 0; r < NR; ++r) {
             real gg = real(0);
 #pragma unroll
-            for (int k = K - 1; k >= 0; --k) gg = fmad(xp[k] * iv[k], gg, d[r][k]);
+            for (int k = K - 1; k >= 0; --k) gg = fmad(cx[k], gg, d[r][k]);
             Gs[r] = gg;
         }
 #pragma unroll
@@ -308,8 +351,8 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             rb_bar(bar_id, G);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                real X = real(0);
-                for (int v = nwl - 1; v > wil; --v) X = fmad(sxH[slot][v], X, sxG[r][slot][v]);
+                // only lanes wil < v < nwl read a published slot
+                const real X = sum8(lane > wil && lane < nwl ? jh * sxG[r][slot][lane] : real(0));
                 Xin[r] = fmad(He, X, Xin[r]);
             }
         }
@@ -318,7 +361,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             real xv = Xin[r];
 #pragma unroll
             for (int k = K - 1; k >= 0; --k) {
-                xv = fmad(xp[k] * iv[k], xv, d[r][k]);
+                xv = fmad(cx[k], xv, d[r][k]);
                 d[r][k] = x[r + 1][k] + xv;
             }
             if (j + r >= jend) continue;  // a row of no slot of this block (or past the field)
@@ -348,7 +391,10 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         if (__any_sync(FULL, a != acls)) {
             if (wide) rb_bar(bar_id, G);  // nobody still reads the previous class's sxF / sxH
             load_class(a);
-            if (wide) rb_bar(bar_id, G);
+            if (wide) {
+                rb_bar(bar_id, G);
+                join_multipliers();
+            }
         }
         const bool two = __all_sync(FULL, t + 1 < band && rowcls[min(j + 1, Nz - 1)] == a);
         if (two) {

@@ -175,3 +175,36 @@ def test_trained_network_gains_speed_over_the_solver_at_its_accuracy():
     assert used and err > 0.5 * float(e1.min())
     np.testing.assert_array_equal(T, s.solve(te[:8]))
     s.close()
+
+
+def test_committed_network_meets_its_recorded_accuracy():
+    """The trained config-5 network shipped with the package (weights written
+    by paper_1912_03744_gb300/train_surrogate.py, its training summary
+    beside them) on fresh solver runs from a seed no training run used: the
+    held-out rise-relative max error stays at the recorded level."""
+    import json
+    import os
+
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver, Surrogate
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    wpath = os.path.join(root, "paper_1912_03744_gb300", "weights", "fno_config5.npy")
+    if not os.path.exists(wpath):
+        pytest.skip("no committed surrogate weights")
+    rec = json.load(open(os.path.splitext(wpath)[0] + ".json"))["held_out"]
+    Df = F.FnoDims()
+    ref = H.config5_reference_problem()
+    probe = HeatSolver(ref, 1.0, precision="fp64")
+    dt = H.DT_FACTOR * probe.tau_exp
+    probe.close()
+    params = H.config5_params(64, seed=11)
+    s = Surrogate(H.config5_problem(params[0]), Df, heater=H.HEATER, dt=dt, steps=2000, max_batch=64)
+    s.set_params(np.load(wpath).astype(np.float32))
+    fields = torch.empty((64, Df.Nz, Df.Nr), dtype=torch.float32, device="cuda")
+    s.solve(params, out=fields)
+    err = s.errors(params, fields)
+    s.close()
+    print(f"committed network on 64 fresh runs: p50 {np.median(err):.4f} (recorded {rec['p50']:.4f}), "
+          f"max {err.max():.4f}")
+    assert np.median(err) <= 2.0 * rec["p50"] + 0.005
+    assert err.max() <= 2.0 * rec["max"] + 0.01
