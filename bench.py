@@ -44,7 +44,7 @@ ELEM = {"fp64": 8, "fp32": 4}
 # capture of this workload (profiles/adi_step_config2_2048x4096_fp32.md):
 # the z-sweep is zsum2 + zcarry2 + zsolve2; None where no capture matches
 # the current kernels.
-TRAFFIC = {("zsweep", "fp32", 2048, 4096): (34.204416e6 + 0.0) + (2.128640e6 + 0.0) + (36.322304e6 + 0.763392e6)}
+TRAFFIC = {("zsweep", "fp32", 2048, 4096): (34.226944e6 + 0.510464e6) + (2.129408e6 + 0.0) + (69.790208e6 + 0.702720e6)}
 
 
 def _peaks():
