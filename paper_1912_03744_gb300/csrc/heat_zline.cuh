@@ -217,16 +217,12 @@ struct ZWalk {
             for (int q = 0; q < E; ++q) zl_tab(pkA, pkB, (size_t)b[q] * Nz + j, e[q]);
         }
     }
-    // right-hand side of row j (then advance the row window)
+    // right-hand side of row j from its left / right neighbours tl, tr of the
+    // lane's first / last column and row j+1 (then advance the row window)
     template <int E>
-    __device__ __forceinline__ void rhs(const Group &G, int p, const real (&e)[E][8], real (&d)[V])
+    __device__ __forceinline__ void rhs_core(real tl, real tr, const real (&nx)[V], const real (&e)[E][8],
+                                             real (&d)[V])
     {
-        real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
-        real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
-        if (hasl) tl = G.hl[p];
-        if (hasr) tr = G.hr[p];
-        if (lo_edge) tl = br_lo;
-        if (hi_edge) tr = br_hi;
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const real(&eq)[8] = e[E == 1 ? 0 : q];
@@ -239,13 +235,96 @@ struct ZWalk {
             } else {
                 // e0 = q, e1 = xm_z, e2 = xp_z
                 real v = fmad(eq[4], tm[q] - x, eq[3]);
-                v = fmad(eq[5], G.nx[p][q] - x, v);
+                v = fmad(eq[5], nx[q] - x, v);
                 v = fmad(ra[q], l - x, v);
                 d[q] = fmad(rb[q], r - x, v);
             }
         }
 #pragma unroll
-        for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = G.nx[p][q];
+        for (int q = 0; q < V; ++q) tm[q] = t[q], t[q] = nx[q];
+    }
+    // the neighbours of the lane's first / last column: the next lanes', a
+    // halo value hl / hr at a warp edge, theta_bc past the field
+    __device__ __forceinline__ void sides(real hl, real hr, real &tl, real &tr) const
+    {
+        tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
+        tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
+        if (hasl) tl = hl;
+        if (hasr) tr = hr;
+        if (lo_edge) tl = br_lo;
+        if (hi_edge) tr = br_hi;
+    }
+    template <int E>
+    __device__ __forceinline__ void rhs(const Group &G, int p, const real (&e)[E][8], real (&d)[V])
+    {
+        real tl, tr;
+        sides(G.hl[p], G.hr[p], tl, tr);
+        rhs_core<E>(tl, tr, G.nx[p], e, d);
+    }
+    // Lean walk of a full interior chunk: rows [j0, j1) with j0 >= 1,
+    // j1 < Nz, (j1 - j0) a multiple of 2 ZQ, every lane inside the field, whole
+    // 16-byte row segments and one row class ucls >= 0.  No row needs a bounds
+    // check, so rows are reached through running pointers, and the one halo
+    // value a lane needs (lane 0: the column left of the warp, lane 31: the
+    // one right of it) is one predicated load.  emit(dst, d, e) gets the
+    // lane's address in row j of the output whose row j0 is at dst.
+    template <int E, typename Emit>
+    __device__ __forceinline__ void walk_full(int ucls, const LineTab<real> &R, real *__restrict__ dst, Emit emit)
+    {
+        const size_t S = (size_t)Nr;
+        row_class(ucls, R);
+        ZVec<real, V>::ld(th + (size_t)(j0 - 1) * S + ib, tm);
+        ZVec<real, V>::ld(th + (size_t)j0 * S + ib, t);
+        const bool hh = hasl || hasr;
+        const real *np = th + (size_t)(j0 + 1) * S + ib;
+        const real *hp = th + (size_t)j0 * S + ib + (lane == 0 ? -1 : V);
+        const real *ep = stg;
+        real nxA[ZQ][V], hA[ZQ], nxB[ZQ][V], hB[ZQ];
+        auto fetch = [&](real(&nx)[ZQ][V], real(&h)[ZQ]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                ZVec<real, V>::ld(np + p * S, nx[p]);
+                h[p] = hh ? __ldg(hp + p * S) : real(0);
+            }
+            np += ZQ * S;
+            hp += ZQ * S;
+        };
+        auto proc = [&](int x, const real(&nx)[ZQ][V], const real(&h)[ZQ]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                real e[E][8], d[V];
+                if constexpr (E == 1) {
+                    if constexpr (sizeof(real) == 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(ep);
+                        const float4 c = *reinterpret_cast<const float4 *>(ep + 4);
+                        e[0][0] = a.x, e[0][1] = a.y, e[0][2] = a.z, e[0][3] = a.w;
+                        e[0][4] = c.x, e[0][5] = c.y, e[0][6] = c.z, e[0][7] = c.w;
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; u += 2) {
+                            const double2 a = *reinterpret_cast<const double2 *>(ep + u);
+                            e[0][u] = a.x, e[0][u + 1] = a.y;
+                        }
+                    }
+                    ep += 8;
+                } else {
+                    tab<E>(x + p, e);
+                }
+                real tl, tr;
+                sides(h[p], h[p], tl, tr);
+                rhs_core<E>(tl, tr, nx[p], e, d);
+                emit(dst, d, e);
+                dst += S;
+            }
+        };
+        fetch(nxA, hA);
+#pragma unroll 1
+        for (int x = j0; x < j1; x += 2 * ZQ) {
+            fetch(nxB, hB);
+            proc(x, nxA, hA);
+            if (x + 2 * ZQ < j1) fetch(nxA, hA);
+            proc(x + ZQ, nxB, hB);
+        }
     }
     // Walk rows [j0, j1) calling emit(j, d, e) with the right-hand side d of
     // row j and its table values e (E = 1: shared by the lane's columns).
@@ -325,14 +404,32 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
             }
         }
     };
+    // the lean walk of a full interior chunk of a warp of one column class
+    // (warp-uniform decision)
+    auto emit_full = [&](real *dst, const real(&d)[V], const auto &e) {
+        constexpr int E = sizeof(e) / sizeof(e[0]);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            dl[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dl[q]);
+            sg[q] = fmad(d[q], e[E == 1 ? 0 : q][7], sg[q]);
+        }
+        ZVec<real, V>::st(dst, dl);
+    };
+    const int ucls = A.ucls[c];
+    const bool full = W.vec && ucls >= 0 && j0 >= 1 && j1 < Nz && (j1 - j0) % (2 * ZQ) == 0 &&
+                      __all_sync(HEAT_FULL_MASK, W.any);
+    real *dst = d0out + (size_t)j0 * Nr + W.ib;
     extern __shared__ __align__(16) unsigned char zs_smem[];
     if (W.warp_uniform()) {
         W.stage(reinterpret_cast<real *>(zs_smem) + (size_t)(threadIdx.x >> 5) * Rc * 8);
         pdl_wait();
-        W.template walk<1>(A.ucls[c], A.R, emit);
+        if (full)
+            W.template walk_full<1>(ucls, A.R, dst, emit_full);
+        else
+            W.template walk<1>(ucls, A.R, emit);
     } else {
         pdl_wait();
-        W.template walk<V>(A.ucls[c], A.R, emit);
+        W.template walk<V>(ucls, A.R, emit);  // (a lean walk here would spill)
     }
     real *__restrict__ zs = A.zs;
     if (W.vec) {
@@ -461,6 +558,59 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
         }
     };
     real da[ZQ][V], ba[ZQ][V], db[ZQ][V], bb[ZQ][V];
+    if (vec && (j1 - j0) % (2 * ZQ) == 0 && __all_sync(HEAT_FULL_MASK, any)) {
+        // a full chunk: no row needs a bounds check; running row pointers
+        const size_t S = (size_t)Nr;
+        const size_t o1 = (size_t)(j1 - 1) * S + ib;
+        const real *dp = out + o1, *tp = th + o1;
+        real *op = out + o1;
+        const real *sp = stg + 2 * (j1 - 1 - j0);
+        auto fetchf = [&](real(&dz)[ZQ][V], real(&bs)[ZQ][V]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                ZVec<real, V>::ld(dp - p * S, dz[p]);
+                if constexpr (!LIT) ZVec<real, V>::ld(tp - p * S, bs[p]);
+            }
+            dp -= ZQ * S;
+            tp -= ZQ * S;
+        };
+        auto procf = [&](int x0, const real(&dz)[ZQ][V], const real(&bs)[ZQ][V]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                real Pj[V], cpj[V];
+                if (wuni) {
+                    const real pv = sp[0], cv = sp[1];
+#pragma unroll
+                    for (int q = 0; q < V; ++q) Pj[q] = pv, cpj[q] = cv;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        const size_t o = (size_t)b[q] * Nz + (x0 - p);
+                        Pj[q] = __ldg(pkB + 4 * o + 2);
+                        cpj[q] = __ldg(pkA + 4 * o + 2);
+                    }
+                }
+                sp -= 2;
+                real o[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
+                    o[q] = LIT ? x[q] : bs[p][q] + x[q];
+                }
+                ZVec<real, V>::st(op, o);
+                op -= S;
+            }
+        };
+        fetchf(da, ba);
+#pragma unroll 1
+        for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
+            fetchf(db, bb);
+            procf(x0, da, ba);
+            if (x0 - 2 * ZQ >= j0) fetchf(da, ba);
+            procf(x0 - ZQ, db, bb);
+        }
+        return;
+    }
     fetch(j1 - 1, da, ba);
 #pragma unroll 1
     for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
