@@ -1374,13 +1374,16 @@ constexpr int kRBlockK = 8, kRBlockRing = 8;
 static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
 {
     constexpr int K = kRBlockK;
+    bool exact = true;  // every line fills its threads exactly, rows 16-byte aligned
     for (int m = 0; m < n; ++m) {
         if (h[m].Nr > 256 * K) return cudaErrorInvalidValue;
         int G = 4;
         while (G * K < h[m].Nr) G <<= 1;
         h[m].G = G;
+        exact = exact && G * K == h[m].Nr && h[m].Nr % 4 == 0;
     }
-    const void *fn = (const void *)rblock_kernel<K, kRBlockRing>;
+    const void *fn = exact ? (const void *)rblock_kernel<K, kRBlockRing, true>
+                           : (const void *)rblock_kernel<K, kRBlockRing, false>;
     const int block = 256;
     const size_t smem = (size_t)kRBlockRing * block * K * sizeof(float);
     cudaError_t e = allow_smem(fn, smem);

@@ -22,7 +22,10 @@
 // cp.async, each thread copying and later reading only its own cells, so the
 // ring needs no block barrier; row j+1..j+NRING-2 are in flight while row j is
 // solved.  The neighbours of a thread's first / last cell come from the next
-// lanes by shuffles, across a warp boundary from global memory.  Wide lines
+// lanes by shuffles, across a warp boundary from global memory.
+// EXACT: the lines fill their threads exactly (Nr = G K, rows 16-byte
+// aligned), so no cell needs a range check; passes away from the z faces
+// read their rows without checks either.  Wide lines
 // join their warps with one named barrier per direction and pass.
 #pragma once
 
@@ -54,7 +57,7 @@ struct RbRows {
     static constexpr int value = N;
 };
 
-template <int K, int NRING>
+template <int K, int NRING, bool EXACT>
 __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *__restrict__ args, int flip)
 {
     using real = float;
@@ -75,7 +78,8 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     if ((int)blockIdx.x * lpb * band >= Nz) return;  // past this instance (block-uniform)
     const int jend = min(Nz, jstart + band);  // rows this slot stores: [jstart, jend)
     const int i0 = g * K;
-    const bool vec = (Nr & 3) == 0;
+    const bool vec = EXACT || (Nr & 3) == 0;
+    static_assert((NRING & (NRING - 1)) == 0, "the ring length is a power of two");
     const unsigned FULL = 0xffffffffu;
     const real bc0 = (real)A.bc.th[0], bc1 = (real)A.bc.th[1];
     const real bc2 = (real)A.bc.th[2], bc3 = (real)A.bc.th[3];
@@ -91,13 +95,13 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
 
     // this thread's K cells of row x into its ring slot (zero past the field)
     auto fetch = [&](int x) {
-        real *dst = ring + (size_t)((x - jstart + 1 + NRING) % NRING) * Np;
+        real *dst = ring + (size_t)((x - jstart + 1) & (NRING - 1)) * Np;  // x >= jstart - 1
         const bool rin = x >= 0 && x < Nz;
         const real *src = th + (size_t)(rin ? x : 0) * Nr;
         if (vec) {
 #pragma unroll
             for (int k = 0; k < K; k += 4) {
-                const bool ok = rin && i0 + k < Nr;
+                const bool ok = rin && (EXACT || i0 + k < Nr);
                 rb_cp16(dst + k, ok ? src + i0 + k : th, ok ? 16 : 0);
             }
         } else {
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     for (int k = 1; k < K; ++k)
         if (i0 + k < Nr) zc1 = colcls[i0 + k];
     unsigned zsel = 0;
-    bool zmany = false;
+    bool zmany = false;  // (then zany: for some lane of the warp)
 #pragma unroll
     for (int k = 1; k < K; ++k)
         if (i0 + k < Nr) {
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             zmany = zmany || (c != zc0 && c != zc1);
         }
 
+    const bool zany = __any_sync(FULL, zmany);
     pdl_wait();
     // prologue: rows jstart-1 .. jstart+NRING-2
     for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
@@ -215,25 +220,35 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         rb_wait<NRING - 2 - NR>();
         // rows j-1 .. j+NR from the ring (ghost rows at the z faces)
         real x[NR + 2][K];
+        auto ld_row = [&](int q, int r) {
+            const real *p = ring + (size_t)((r - jstart + 1) & (NRING - 1)) * Np;
 #pragma unroll
-        for (int q = 0; q < NR + 2; ++q) {
-            const int r = j - 1 + q;
-            const real *p = ring + (size_t)((r - jstart + 1 + NRING) % NRING) * Np;
-            if (r < 0 || r >= Nz) {
+            for (int k = 0; k < K; k += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(p + k);
+                x[q][k] = v.x, x[q][k + 1] = v.y, x[q][k + 2] = v.z, x[q][k + 3] = v.w;
+            }
+        };
+        if (__all_sync(FULL, j >= 1 && j + NR < Nz)) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) x[q][k] = r < 0 ? bc2 : bc3;
-            } else {
+            for (int q = 0; q < NR + 2; ++q) ld_row(q, j - 1 + q);
+        } else {
 #pragma unroll
-                for (int k = 0; k < K; k += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(p + k);
-                    x[q][k] = v.x, x[q][k + 1] = v.y, x[q][k + 2] = v.z, x[q][k + 3] = v.w;
+            for (int q = 0; q < NR + 2; ++q) {
+                const int r = j - 1 + q;
+                if (r < 0 || r >= Nz) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) x[q][k] = r < 0 ? bc2 : bc3;
+                } else {
+                    ld_row(q, r);
                 }
-                if (i0 + K > Nr)
-#pragma unroll
-                    for (int k = 0; k < K; ++k)
-                        if (i0 + k >= Nr) x[q][k] = bc1;  // ghost past the outer r face
             }
         }
+        if (!EXACT && i0 + K > Nr)
+#pragma unroll
+            for (int q = 0; q < NR + 2; ++q)
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (i0 + k >= Nr && j - 1 + q >= 0 && j - 1 + q < Nz) x[q][k] = bc1;  // ghost past the outer r face
         // right-hand sides
         real d[NR][K];
 #pragma unroll
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             const real *xr = x[r + 1];
             real nl = __shfl_up_sync(FULL, xr[K - 1], 1, W);
             real nrt = __shfl_down_sync(FULL, xr[0], 1, W);
-            if (ls == 0) nl = (i0 > 0 && i0 - 1 < Nr) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
+            if (ls == 0) nl = (i0 > 0 && (EXACT || i0 - 1 < Nr)) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
             if (ls == W - 1) nrt = (i0 + K < Nr) ? th[(size_t)jr * Nr + i0 + K] : bc1;
             const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
             const real zmA = Z.xm[zo], zpA = Z.xp[zo], zmB = Z.xm[zo1], zpB = Z.xp[zo1];
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
                 const real zz = fmad(zp, x[r + 2][k] - xc, zm * (x[r][k] - xc));
                 d[r][k] = fmad(iv[k], zz, v);
             }
-            if (zmany) {
+            if (zany) {
                 // the chunk crosses a column-class boundary: per-cell z coefficients
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             }
             if (j + r >= jend) continue;  // a row of no slot of this block (or past the field)
             real *orow = out + (size_t)(j + r) * Nr;
-            if (vec && i0 + K <= Nr) {
+            if (EXACT || (vec && i0 + K <= Nr)) {
 #pragma unroll
                 for (int k = 0; k < K; k += 4)
                     *reinterpret_cast<float4 *>(orow + i0 + k) = make_float4(d[r][k], d[r][k + 1], d[r][k + 2], d[r][k + 3]);
