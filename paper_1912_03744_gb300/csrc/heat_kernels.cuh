@@ -1495,7 +1495,7 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
                 : (const void *)zsolve_kernel<real, V, MODE>;
     c.grid = dim3((groups + cw - 1) / cw, maxNch, n);
     c.block = dim3(32 * cw, 1, 1);
-    c.smem = lean ? (size_t)cw * maxRc * 2 * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
+    c.smem = lean ? (size_t)cw * ZNC * maxRc * 2 * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
     c.flip = true;
     if ((e = allow_smem(c.fn, c.smem)) != cudaSuccess) return e;
     out.push_back(a);

@@ -20,6 +20,8 @@
 // classes (a layer interface) reads them per column.
 #pragma once
 
+#include <type_traits>
+
 #include "heat_internal.h"
 
 namespace heat {
@@ -69,6 +71,49 @@ __device__ __forceinline__ void zl_tab(const real *__restrict__ pkA, const real 
             const double2 b = __ldg(reinterpret_cast<const double2 *>(pkB + 4 * o + u));
             e[u] = a.x, e[u + 1] = a.y, e[4 + u] = b.x, e[5 + u] = b.y;
         }
+    }
+}
+
+// Column classes staged per warp by the solve pass.
+constexpr int ZNC = 4;
+
+// The distinct column classes of the warp's columns inside the field, in
+// order of discovery, into slot[0 .. ns-1]; false when there are more than
+// ZNC.  slot[] and ns come out the same in every lane.
+template <int V>
+__device__ __forceinline__ bool zl_classes(const int (&b)[V], int ib, int Nr, int (&slot)[ZNC], int &ns)
+{
+#pragma unroll
+    for (int s = 0; s < ZNC; ++s) slot[s] = -1;
+    ns = 0;
+#pragma unroll
+    for (int round = 0; round <= ZNC; ++round) {
+        int mine = -1;
+#pragma unroll
+        for (int q = V - 1; q >= 0; --q) {
+            bool known = false;
+#pragma unroll
+            for (int s = 0; s < ZNC; ++s) known = known || b[q] == slot[s];
+            if (ib + q < Nr && !known) mine = b[q];
+        }
+        const unsigned bal = __ballot_sync(HEAT_FULL_MASK, mine >= 0);
+        if (bal == 0) return true;
+        if (round == ZNC) return false;
+        slot[round] = __shfl_sync(HEAT_FULL_MASK, mine, __ffs(bal) - 1);
+        ns = round + 1;
+    }
+    return false;
+}
+// slot of each of the lane's columns (0 past the field)
+template <int V>
+__device__ __forceinline__ void zl_slots(const int (&b)[V], int ib, int Nr, const int (&slot)[ZNC], int (&sq)[V])
+{
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        sq[q] = 0;
+#pragma unroll
+        for (int s = 1; s < ZNC; ++s)
+            if (ib + q < Nr && b[q] == slot[s]) sq[q] = s;
     }
 }
 
@@ -481,16 +526,29 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
     for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
     const int bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
     const bool wuni = __all_sync(HEAT_FULL_MASK, !any || (uni && b[0] == bw));
-    // staged (P_j, cp_j) of the chunk's rows for a warp of one column class
+    // staged (P_j, cp_j) of the chunk's rows for each of the warp's (at most
+    // ZNC) column classes, [slot][Rc][2]; slot 0 is bw in a warp of one class
+    int slot[ZNC], ns;
+    const bool few = zl_classes(b, ib, Nr, slot, ns);
     extern __shared__ __align__(16) unsigned char zl_smem[];
-    real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * Rc * 2;
-    if (wuni) {
-        for (int r = lane; r < j1 - j0; r += 32) {
-            const size_t o = (size_t)bw * Nz + j0 + r;
-            stg[2 * r] = __ldg(pkB + 4 * o + 2);
-            stg[2 * r + 1] = __ldg(pkA + 4 * o + 2);
+    real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * ZNC * Rc * 2;
+    int off[V];
+    if (few) {
+        for (int u = lane; u < ns * (j1 - j0); u += 32) {
+            const int s = u / (j1 - j0), r = u - s * (j1 - j0);
+            int cs = slot[0];
+#pragma unroll
+            for (int k = 1; k < ZNC; ++k)
+                if (s == k) cs = slot[k];
+            const size_t o = (size_t)cs * Nz + j0 + r;
+            stg[((size_t)s * Rc + r) * 2] = __ldg(pkB + 4 * o + 2);
+            stg[((size_t)s * Rc + r) * 2 + 1] = __ldg(pkA + 4 * o + 2);
         }
         __syncwarp();
+        int sq[V];
+        zl_slots(b, ib, Nr, slot, sq);
+#pragma unroll
+        for (int q = 0; q < V; ++q) off[q] = sq[q] * Rc * 2;
     }
     pdl_wait();
     const real *__restrict__ zc = A.zc;
@@ -558,56 +616,93 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
         }
     };
     real da[ZQ][V], ba[ZQ][V], db[ZQ][V], bb[ZQ][V];
-    if (vec && (j1 - j0) % (2 * ZQ) == 0 && __all_sync(HEAT_FULL_MASK, any)) {
-        // a full chunk: no row needs a bounds check; running row pointers
+    if (few && (j1 - j0) % (2 * ZQ) == 0) {
+        // a full chunk: no row needs a bounds check; running row pointers.
+        // TM = 1: one class (one staged (P, cp) pair per row), else per
+        // column; VEC: whole 16-byte row segments, else per column with
+        // range checks
         const size_t S = (size_t)Nr;
         const size_t o1 = (size_t)(j1 - 1) * S + ib;
-        const real *dp = out + o1, *tp = th + o1;
-        real *op = out + o1;
-        const real *sp = stg + 2 * (j1 - 1 - j0);
-        auto fetchf = [&](real(&dz)[ZQ][V], real(&bs)[ZQ][V]) {
+        auto lean = [&](auto tm_tag, auto vec_tag) {
+            constexpr int TM = decltype(tm_tag)::value;
+            constexpr bool VEC = decltype(vec_tag)::value;
+            const real *dp = out + o1, *tp = th + o1;
+            real *op = out + o1;
+            int ro = 2 * (j1 - 1 - j0);
+            auto ld = [&](const real *p, real(&v)[V]) {
+                if constexpr (VEC) {
+                    if (any) {
+                        ZVec<real, V>::ld(p, v);
+                    } else {
 #pragma unroll
-            for (int p = 0; p < ZQ; ++p) {
-                ZVec<real, V>::ld(dp - p * S, dz[p]);
-                if constexpr (!LIT) ZVec<real, V>::ld(tp - p * S, bs[p]);
-            }
-            dp -= ZQ * S;
-            tp -= ZQ * S;
-        };
-        auto procf = [&](int x0, const real(&dz)[ZQ][V], const real(&bs)[ZQ][V]) {
-#pragma unroll
-            for (int p = 0; p < ZQ; ++p) {
-                real Pj[V], cpj[V];
-                if (wuni) {
-                    const real pv = sp[0], cv = sp[1];
-#pragma unroll
-                    for (int q = 0; q < V; ++q) Pj[q] = pv, cpj[q] = cv;
+                        for (int q = 0; q < V; ++q) v[q] = real(0);
+                    }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < V; ++q) {
-                        const size_t o = (size_t)b[q] * Nz + (x0 - p);
-                        Pj[q] = __ldg(pkB + 4 * o + 2);
-                        cpj[q] = __ldg(pkA + 4 * o + 2);
-                    }
+                    for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? __ldg(p + q) : real(0);
                 }
-                sp -= 2;
-                real o[V];
+            };
+            auto fetchf = [&](real(&dz)[ZQ][V], real(&bs)[ZQ][V]) {
 #pragma unroll
-                for (int q = 0; q < V; ++q) {
-                    x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
-                    o[q] = LIT ? x[q] : bs[p][q] + x[q];
+                for (int p = 0; p < ZQ; ++p) {
+                    ld(dp - p * S, dz[p]);
+                    if constexpr (!LIT) ld(tp - p * S, bs[p]);
                 }
-                ZVec<real, V>::st(op, o);
-                op -= S;
+                dp -= ZQ * S;
+                tp -= ZQ * S;
+            };
+            auto procf = [&](const real(&dz)[ZQ][V], const real(&bs)[ZQ][V]) {
+#pragma unroll
+                for (int p = 0; p < ZQ; ++p) {
+                    real Pj[V], cpj[V];
+                    if constexpr (TM == 1) {
+                        const real pv = stg[ro], cv = stg[ro + 1];
+#pragma unroll
+                        for (int q = 0; q < V; ++q) Pj[q] = pv, cpj[q] = cv;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) Pj[q] = stg[off[q] + ro], cpj[q] = stg[off[q] + ro + 1];
+                    }
+                    ro -= 2;
+                    real o[V];
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
+                        o[q] = LIT ? x[q] : bs[p][q] + x[q];
+                    }
+                    if constexpr (VEC) {
+                        if (any) ZVec<real, V>::st(op, o);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < V; ++q)
+                            if (ib + q < Nr) op[q] = o[q];
+                    }
+                    op -= S;
+                }
+            };
+            fetchf(da, ba);
+#pragma unroll 1
+            for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
+                fetchf(db, bb);
+                procf(da, ba);
+                if (x0 - 2 * ZQ >= j0) fetchf(da, ba);
+                procf(db, bb);
             }
         };
-        fetchf(da, ba);
-#pragma unroll 1
-        for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
-            fetchf(db, bb);
-            procf(x0, da, ba);
-            if (x0 - 2 * ZQ >= j0) fetchf(da, ba);
-            procf(x0 - ZQ, db, bb);
+        using One = std::integral_constant<int, 1>;
+        using Many = std::integral_constant<int, ZNC>;
+        using Vec = std::integral_constant<bool, true>;
+        using Sca = std::integral_constant<bool, false>;
+        if (ns == 1) {
+            if (vec)
+                lean(One(), Vec());
+            else
+                lean(One(), Sca());
+        } else {
+            if (vec)
+                lean(Many(), Vec());
+            else
+                lean(Many(), Sca());
         }
         return;
     }
@@ -650,7 +745,7 @@ __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<rea
     const int m = (nch + ZSEG2 - 1) / ZSEG2;
     const int c0 = sgm * m;
     const size_t st = (size_t)2 * Nr;
-    real Bv[ZMAXM], Gv[ZMAXM], Fv[ZMAXM], Hv[ZMAXM];
+    real Bv[ZMAXM], Gv[ZMAXM], Fv[ZMAXM], Hv[ZMAXM], GPv[ZMAXM];
 #pragma unroll
     for (int u = 0; u < ZMAXM; ++u) {
         const int c = c0 + u;
@@ -659,6 +754,7 @@ __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<rea
         Gv[u] = ok ? zs[c * st + Nr + i] : real(0);
         Fv[u] = ok ? chb[c * 4] : real(1);
         Hv[u] = ok ? chb[c * 4 + 1] : real(1);
+        if constexpr (sizeof(real) == 4) GPv[u] = ok ? chb[c * 4 + 2] : real(0);  // (FP64: no registers left)
     }
     // forward: D_c = B_c + F_c D_{c-1}
     real F = real(1), B = real(0);
@@ -679,7 +775,10 @@ __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<rea
         const bool ok = col && u < m && c < nch;
         if (ok) {
             zc[c * st + i] = D;
-            Gv[u] = fmad(chb[c * 4 + 2], D, Gv[u]);
+            if constexpr (sizeof(real) == 4)
+                Gv[u] = fmad(GPv[u], D, Gv[u]);
+            else
+                Gv[u] = fmad(chb[c * 4 + 2], D, Gv[u]);
         }
         D = fmad(Fv[u], D, Bv[u]);
     }
