@@ -124,6 +124,18 @@ int upload_zpart(heat_ctx *ctx)
         HEAT_CHECK(cudaMalloc(&z.ucls, u.size() * sizeof(int)));
         HEAT_CHECK(cudaMemcpyAsync(z.ucls, u.data(), u.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     }
+    {
+        // (FP32 increment path only: the FP64 passes spill with the tile
+        // bookkeeping and ran slower tiled; the refined path has no lean passes)
+        std::vector<int> t;
+        if (ctx->precision == HEAT_FP32) t = z_tiles(ctx->g.colcls, ctx->g.Nr, 4);
+        if (z.tiles) cudaFree(z.tiles), z.tiles = nullptr;
+        z.n_tiles = (int)t.size() / 4;
+        if (z.n_tiles) {
+            HEAT_CHECK(cudaMalloc(&z.tiles, t.size() * sizeof(int)));
+            HEAT_CHECK(cudaMemcpyAsync(z.tiles, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
     const size_t nsum = (size_t)z.n_chunks * 4 * ctx->g.Nr;  // summaries [nch][2][Nr] + carries [nch][2][Nr]
     if (ctx->precision == HEAT_FP64) {
         int st = upload_zpart_t<double>(ctx, z.pk64, z.ch64);
@@ -195,7 +207,7 @@ void free_ctx(heat_ctx *ctx)
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
                     ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,
-                    ctx->d_args,   ctx->d_rl,       ctx->d_rlz};
+                    ctx->d_args,   ctx->d_rl,       ctx->d_rlz,      ctx->zp.tiles};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;

@@ -118,6 +118,8 @@ struct SweepArgs {
     BcVals bc;
     const real *pkA, *pkB, *chk;
     const int *ucls;
+    const int4 *ztile;        // z-sweep column tiles {wb, lo, hi, 0} (n_ztile of them; 0: warps of 32 V columns)
+    int n_ztile;
     real *zs, *zc, *rho;
     real *f0, *f1;
 };
@@ -184,7 +186,19 @@ struct ZPart {
     double *pk64 = nullptr, *ch64 = nullptr;  // device
     float *pk32 = nullptr, *ch32 = nullptr;   // device (FP32 paths)
     int *ucls = nullptr;                      // device: row class of chunk c if all its rows share it, else -1
+    int4 *tiles = nullptr;                    // device: column tiles of the lean z passes (see z_tiles)
+    int n_tiles = 0;
 };
+
+// Column tiles of the lean z passes, one warp each: the columns [lo, hi) of
+// one column class, the warp's lanes holding V-column row segments from the
+// V-aligned column wb <= lo (lanes may read columns outside [lo, hi), they
+// store only inside).  A warp then never straddles a layer interface, where
+// it would read its tables per column.  Returned only where some warp of
+// 32 V columns from column 0 would straddle one and the tiles cost at most an
+// eighth more warps; else empty.  Used for single instances (a batch plan
+// drops them).
+std::vector<int> z_tiles(const std::vector<int> &colcls, int Nr, int V);
 
 // Rows per z chunk (one warp walks a chunk of its columns): 32, or more
 // (a multiple of 4) so that a column has at most 256 chunks.

@@ -1469,10 +1469,17 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
         maxRc = h[m].Rc > maxRc ? h[m].Rc : maxRc;
         maxNch = h[m].nch > maxNch ? h[m].nch : maxNch;
     }
-    const int groups = (maxNr + COLS - 1) / COLS;
     constexpr bool lean = MODE == MODE_LIT || MODE == MODE_DELTA;  // heat_zline.cuh passes
+    // warps per instance: one per 32 V columns, or (lean passes) one per
+    // column tile where the instance has a tile table
+    int groups = (maxNr + COLS - 1) / COLS;
+    bool tiled = false;
+    for (int m = 0; m < n && lean; ++m)
+        if (h[m].n_ztile > 0) tiled = true, groups = h[m].n_ztile > groups ? h[m].n_ztile : groups;
     Launch a, b, c;
-    constexpr int SWPB = 4;
+    // one warp per block for a (single) tiled instance: its tiles x chunks
+    // then still fit in one wave of 16 resident warps per SM
+    const int SWPB = tiled ? 1 : 4;
     a.fn = lean ? (const void *)zsum2_kernel<real, V, lean ? MODE : MODE_DELTA> : (const void *)zsum_kernel<real, V, MODE>;
     a.grid = dim3((groups + SWPB - 1) / SWPB, maxNch, n);
     a.block = dim3(32 * SWPB, 1, 1);
@@ -1489,8 +1496,9 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     int wpb = tu.zwpb;
     if (wpb != 1 && wpb != 2) wpb = (size_t)maxRc * COLS * sizeof(real) <= 32 * 1024 ? 2 : 1;
     tu.zwpb = wpb;
-    // the lean solve keeps no forward results: 4 warps per block, staged (P, cp) rows only
-    const int cw = lean ? 4 : wpb;
+    // the lean solve keeps no forward results: 4 warps per block (as the
+    // summary pass: 1 for a single tiled instance), staged (P, cp) rows only
+    const int cw = lean ? SWPB : wpb;
     c.fn = lean ? (const void *)zsolve2_kernel<real, V, lean ? MODE : MODE_DELTA>
                 : (const void *)zsolve_kernel<real, V, MODE>;
     c.grid = dim3((groups + cw - 1) / cw, maxNch, n);
@@ -1510,6 +1518,10 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
 {
     plan = SweepPlan();
     Tuning tu = req;
+    // column tiles only for a single instance: in a batch the widest
+    // member's tile count would set every member's grid width
+    if (n > 1)
+        for (int m = 0; m < n; ++m) h[m].n_ztile = 0, h[m].ztile = nullptr;
     Launch r;
     cudaError_t e = cudaErrorInvalidValue;
     bool line_tables = MODE == MODE_LIT || MODE == MODE_DELTA;

@@ -452,4 +452,32 @@ bool build_rline(const heat_ctx *ctx, int K, size_t max_buf_bytes, int &LW, int 
     return true;
 }
 
+std::vector<int> z_tiles(const std::vector<int> &colcls, int Nr, int V)
+{
+    const int COLS = 32 * V;
+    const int plain = (Nr + COLS - 1) / COLS;
+    bool straddle = false;
+    for (int g = 0; g < plain && !straddle; ++g)
+        for (int i = g * COLS + 1; i < std::min(Nr, (g + 1) * COLS); ++i)
+            if (colcls[i] != colcls[i - 1]) {
+                straddle = true;
+                break;
+            }
+    std::vector<int> t;
+    if (!straddle) return t;
+    for (int s0 = 0; s0 < Nr;) {
+        int s1 = s0 + 1;
+        while (s1 < Nr && colcls[s1] == colcls[s0]) ++s1;
+        for (int wb = s0 / V * V; wb < s1; wb += COLS) {
+            t.push_back(wb);
+            t.push_back(std::max(s0, wb));
+            t.push_back(std::min(s1, wb + COLS));
+            t.push_back(0);
+        }
+        s0 = s1;
+    }
+    if ((int)t.size() / 4 > plain + std::max(1, plain / 8)) t.clear();
+    return t;
+}
+
 }  // namespace heat

@@ -54,6 +54,8 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
     a.Z64 = ctx->dZ.full;
     for (int f = 0; f < 4; ++f) a.bc.th[f] = ctx->theta_bc[f];
     a.ucls = ctx->zp.ucls;
+    a.ztile = ctx->zp.tiles;
+    a.n_ztile = ctx->zp.n_tiles;
     a.zc = a.zs + (size_t)2 * a.nch * a.Nr;
     a.rl = RLine<real>{};
     if (ctx->rl_LW > 0) {

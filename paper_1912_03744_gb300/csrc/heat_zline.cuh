@@ -77,11 +77,11 @@ __device__ __forceinline__ void zl_tab(const real *__restrict__ pkA, const real 
 // Column classes staged per warp by the solve pass.
 constexpr int ZNC = 4;
 
-// The distinct column classes of the warp's columns inside the field, in
-// order of discovery, into slot[0 .. ns-1]; false when there are more than
-// ZNC.  slot[] and ns come out the same in every lane.
+// The distinct column classes of the columns the warp stores (bits of
+// smask), in order of discovery, into slot[0 .. ns-1]; false when there are
+// more than ZNC.  slot[] and ns come out the same in every lane.
 template <int V>
-__device__ __forceinline__ bool zl_classes(const int (&b)[V], int ib, int Nr, int (&slot)[ZNC], int &ns)
+__device__ __forceinline__ bool zl_classes(const int (&b)[V], unsigned smask, int (&slot)[ZNC], int &ns)
 {
 #pragma unroll
     for (int s = 0; s < ZNC; ++s) slot[s] = -1;
@@ -94,7 +94,7 @@ __device__ __forceinline__ bool zl_classes(const int (&b)[V], int ib, int Nr, in
             bool known = false;
 #pragma unroll
             for (int s = 0; s < ZNC; ++s) known = known || b[q] == slot[s];
-            if (ib + q < Nr && !known) mine = b[q];
+            if (((smask >> q) & 1u) && !known) mine = b[q];
         }
         const unsigned bal = __ballot_sync(HEAT_FULL_MASK, mine >= 0);
         if (bal == 0) return true;
@@ -104,17 +104,44 @@ __device__ __forceinline__ bool zl_classes(const int (&b)[V], int ib, int Nr, in
     }
     return false;
 }
-// slot of each of the lane's columns (0 past the field)
+// slot of each of the lane's columns (0 for those it does not store)
 template <int V>
-__device__ __forceinline__ void zl_slots(const int (&b)[V], int ib, int Nr, const int (&slot)[ZNC], int (&sq)[V])
+__device__ __forceinline__ void zl_slots(const int (&b)[V], unsigned smask, const int (&slot)[ZNC], int (&sq)[V])
 {
 #pragma unroll
     for (int q = 0; q < V; ++q) {
         sq[q] = 0;
 #pragma unroll
         for (int s = 1; s < ZNC; ++s)
-            if (ib + q < Nr && b[q] == slot[s]) sq[q] = s;
+            if (((smask >> q) & 1u) && b[q] == slot[s]) sq[q] = s;
     }
+}
+
+// The column tile of warp grp of an instance: its lanes' first column wb and
+// the columns [lo, hi) it stores (the instance's tile table, else warps of
+// 32 V columns from column 0); false past the last tile.
+template <typename real, int V>
+__device__ __forceinline__ bool zl_tile(const SweepArgs<real> &A, int grp, int &wb, int &lo, int &hi)
+{
+    if (A.n_ztile > 0) {
+        if (grp >= A.n_ztile) return false;
+        const int4 t = A.ztile[grp];
+        wb = t.x, lo = t.y, hi = t.z;
+        return true;
+    }
+    wb = grp * 32 * V;
+    lo = wb, hi = min(A.Nr, wb + 32 * V);
+    return wb < A.Nr;
+}
+// bits q of the lane's columns ib + q inside [lo, hi)
+template <int V>
+__device__ __forceinline__ unsigned zl_mask(int ib, int lo, int hi)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+        if (ib + q >= lo && ib + q < hi) m |= 1u << q;
+    return m;
 }
 
 // Per-lane state of a z walk over rows [j0, j1) of the lane's V columns.
@@ -127,6 +154,8 @@ struct ZWalk {
     const int *__restrict__ rowcls;
     int Nr, Nz, ib, lane, j0, j1;
     bool any, vec, uni, hasl, hasr, lo_edge, hi_edge;
+    unsigned smask;                   // the lane's columns this walk stores (its tile's)
+    bool sfull;                       // all V of them
     int b[V];
     int acur;
     real ra[V], rb[V], rc[V], rd[V];  // increment: xm, xp of the row class; literal: am, ap, ad, sd
@@ -135,19 +164,25 @@ struct ZWalk {
     const real *stg = nullptr;        // the chunk's staged table rows [j1 - j0][8] (uniform warps)
     int bw = 0;                       // the warp's column class when it has one
 
+    // any: the lane has columns inside the field (it reads them: they are
+    // neighbours); smask: the columns of its tile [lo, hi), the ones it stores
+    // and whose class counts
     __device__ __forceinline__ void init(const SweepArgs<real> &A, const real *th_, int ib_, int lane_, int j0_,
-                                         int j1_)
+                                         int j1_, int lo, int hi)
     {
         th = th_, pkA = A.pkA, pkB = A.pkB, rowcls = A.rowcls;
         Nr = A.Nr, Nz = A.Nz, ib = ib_, lane = lane_, j0 = j0_, j1 = j1_;
         any = ib < Nr;
         vec = (Nr % V) == 0;
+        smask = zl_mask<V>(ib, lo, hi);
+        sfull = smask == (1u << V) - 1;
         lo_edge = ib == 0;
         hi_edge = ib < Nr && ib + V >= Nr;
         hasl = lane == 0 && ib > 0 && ib - 1 < Nr;
         hasr = lane == 31 && ib + V < Nr;
+        const int i1 = smask ? ib + __ffs(smask) - 1 : 0;  // the lane's first stored column
 #pragma unroll
-        for (int q = 0; q < V; ++q) b[q] = ib + q < Nr ? A.colcls[ib + q] : (any ? A.colcls[ib] : 0);
+        for (int q = 0; q < V; ++q) b[q] = A.colcls[(smask >> q) & 1u ? ib + q : i1];
         uni = true;
 #pragma unroll
         for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
@@ -211,13 +246,24 @@ struct ZWalk {
             }
         }
     }
-    // True (for every lane) when every column of the warp inside the field has
-    // lane 0's column class bw; lanes past the field then compute with bw too
-    // and store nothing.
+    // True (for every lane) when every column the warp stores has lane 0's
+    // column class bw (lane 0 always stores one); the other columns are then
+    // computed with bw too and not stored.
     __device__ __forceinline__ bool warp_uniform()
     {
         bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
-        return __all_sync(HEAT_FULL_MASK, !any || (uni && b[0] == bw));
+        return __all_sync(HEAT_FULL_MASK, !smask || (uni && b[0] == bw));
+    }
+    // store the lane's V values at p (its tile's columns)
+    __device__ __forceinline__ void put(real *p, const real (&v)[V]) const
+    {
+        if (vec && sfull) {
+            ZVec<real, V>::st(p, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+                if ((smask >> q) & 1u) p[q] = v[q];
+        }
     }
     // Stage the chunk's table rows of class bw (a uniform warp) in the warp's
     // shared-memory slice buf [j1 - j0][8]: one row per lane per pass, all
@@ -422,12 +468,13 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
     if ((int)blockIdx.y >= A.nch) return;
     const int lane = threadIdx.x & 31;
     const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (grp * 32 * V >= Nr) return;  // whole warp past the field (warp-uniform)
+    int wb, lo, hi;
+    if (!zl_tile<real, V>(A, grp, wb, lo, hi)) return;  // no column tile (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
     real *__restrict__ d0out = flip ? A.f0 : A.f1;
     ZWalk<real, V, MODE> W;
-    W.init(A, flip ? A.f1 : A.f0, grp * 32 * V + lane * V, lane, j0, j1);
+    W.init(A, flip ? A.f1 : A.f0, wb + lane * V, lane, j0, j1, lo, hi);
     real dl[V], sg[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) dl[q] = sg[q] = real(0);
@@ -438,16 +485,7 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
             dl[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dl[q]);
             sg[q] = fmad(d[q], e[E == 1 ? 0 : q][7], sg[q]);
         }
-        if (W.any) {
-            real *row = d0out + (size_t)j * Nr + W.ib;
-            if (W.vec) {
-                ZVec<real, V>::st(row, dl);
-            } else {
-#pragma unroll
-                for (int q = 0; q < V; ++q)
-                    if (W.ib + q < Nr) row[q] = dl[q];
-            }
-        }
+        W.put(d0out + (size_t)j * Nr + W.ib, dl);
     };
     // the lean walk of a full interior chunk of a warp of one column class
     // (warp-uniform decision)
@@ -458,7 +496,7 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
             dl[q] = fmad(d[q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dl[q]);
             sg[q] = fmad(d[q], e[E == 1 ? 0 : q][7], sg[q]);
         }
-        ZVec<real, V>::st(dst, dl);
+        W.put(dst, dl);
     };
     const int ucls = A.ucls[c];
     const bool full = W.vec && ucls >= 0 && j0 >= 1 && j1 < Nz && (j1 - j0) % (2 * ZQ) == 0 &&
@@ -477,19 +515,8 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
         W.template walk<V>(ucls, A.R, emit);  // (a lean walk here would spill)
     }
     real *__restrict__ zs = A.zs;
-    if (W.vec) {
-        if (W.any) {
-            ZVec<real, V>::st(zs + ((size_t)c * 2) * Nr + W.ib, dl);
-            ZVec<real, V>::st(zs + ((size_t)c * 2 + 1) * Nr + W.ib, sg);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-            if (W.ib + q < Nr) {
-                zs[((size_t)c * 2) * Nr + W.ib + q] = dl[q];
-                zs[((size_t)c * 2 + 1) * Nr + W.ib + q] = sg[q];
-            }
-    }
+    W.put(zs + ((size_t)c * 2) * Nr + W.ib, dl);
+    W.put(zs + ((size_t)c * 2 + 1) * Nr + W.ib, sg);
 }
 
 // Pass 3: every (column, chunk) walked back from its carries: with
@@ -507,29 +534,42 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
     real *__restrict__ out = flip ? A.f0 : A.f1;  // holds d0 on entry
     const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     if ((int)blockIdx.y >= A.nch) return;
-    constexpr int COLS = 32 * V;
     constexpr bool LIT = MODE == MODE_LIT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int grp = blockIdx.x * (blockDim.x >> 5) + w;
-    if (grp * COLS >= Nr) return;  // whole warp past the field (warp-uniform)
+    int wb, lo, hi;
+    if (!zl_tile<real, V>(A, grp, wb, lo, hi)) return;  // no column tile (warp-uniform)
     const int c = blockIdx.y;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
-    const int ib = grp * COLS + lane * V;
+    const int ib = wb + lane * V;
+    // any: columns inside the field (read); smask: the tile's (stored)
     const bool any = ib < Nr, vec = (Nr % V) == 0;
+    const unsigned smask = zl_mask<V>(ib, lo, hi);
+    const bool sfull = smask == (1u << V) - 1;
     const real *__restrict__ pkA = A.pkA;
     const real *__restrict__ pkB = A.pkB;
     int b[V];
+    const int i1 = smask ? ib + __ffs(smask) - 1 : 0;  // the lane's first stored column
 #pragma unroll
-    for (int q = 0; q < V; ++q) b[q] = ib + q < Nr ? A.colcls[ib + q] : (any ? A.colcls[ib] : 0);
+    for (int q = 0; q < V; ++q) b[q] = A.colcls[(smask >> q) & 1u ? ib + q : i1];
     bool uni = true;
 #pragma unroll
     for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
     const int bw = __shfl_sync(HEAT_FULL_MASK, b[0], 0);
-    const bool wuni = __all_sync(HEAT_FULL_MASK, !any || (uni && b[0] == bw));
+    const bool wuni = __all_sync(HEAT_FULL_MASK, !smask || (uni && b[0] == bw));
+    auto put = [&](real *p, const real(&v)[V]) {
+        if (vec && sfull) {
+            ZVec<real, V>::st(p, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+                if ((smask >> q) & 1u) p[q] = v[q];
+        }
+    };
     // staged (P_j, cp_j) of the chunk's rows for each of the warp's (at most
     // ZNC) column classes, [slot][Rc][2]; slot 0 is bw in a warp of one class
     int slot[ZNC], ns;
-    const bool few = zl_classes(b, ib, Nr, slot, ns);
+    const bool few = zl_classes(b, smask, slot, ns);
     extern __shared__ __align__(16) unsigned char zl_smem[];
     real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * ZNC * Rc * 2;
     int off[V];
@@ -546,7 +586,7 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
         }
         __syncwarp();
         int sq[V];
-        zl_slots(b, ib, Nr, slot, sq);
+        zl_slots(b, smask, slot, sq);
 #pragma unroll
         for (int q = 0; q < V; ++q) off[q] = sq[q] * Rc * 2;
     }
@@ -555,7 +595,7 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
     real D[V], x[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-        const bool in = ib + q < Nr;
+        const bool in = (smask >> q) & 1u;
         D[q] = in ? zc[((size_t)c * 2) * Nr + ib + q] : real(0);
         x[q] = in ? zc[((size_t)c * 2 + 1) * Nr + ib + q] : real(0);
     }
@@ -602,16 +642,7 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
                     x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
                     o[q] = LIT ? x[q] : bs[p][q] + x[q];
                 }
-                if (any) {
-                    real *orow = out + (size_t)j * Nr + ib;
-                    if (vec) {
-                        ZVec<real, V>::st(orow, o);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < V; ++q)
-                            if (ib + q < Nr) orow[q] = o[q];
-                    }
-                }
+                put(out + (size_t)j * Nr + ib, o);
             }
         }
     };
@@ -670,13 +701,7 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
                         x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
                         o[q] = LIT ? x[q] : bs[p][q] + x[q];
                     }
-                    if constexpr (VEC) {
-                        if (any) ZVec<real, V>::st(op, o);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < V; ++q)
-                            if (ib + q < Nr) op[q] = o[q];
-                    }
+                    put(op, o);
                     op -= S;
                 }
             };
