@@ -41,11 +41,11 @@ UNIT = "cell-steps/s"
 WORKLOAD = "config2: five-region layered cell 2048x4096, seed 2, dt=50*tau_exp"
 ELEM = {"fp64": 8, "fp32": 4}
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
-# (profiles/adi_step_config2_2048x4096_fp32.md): the r-sweep kernel, and the
-# z-sweep's zsum2 + zcarry2 + zsolve2; None where no capture matches the
-# current kernels.
-TRAFFIC = {("rsweep", "fp32", 2048, 4096): 34.176256e6 + 0.316160e6,
-           ("zsweep", "fp32", 2048, 4096): (34.226944e6 + 0.510464e6) + (2.129408e6 + 0.0) + (69.790208e6 + 0.702720e6)}
+# (--set full, one step's launches): the r-sweep kernel, and the z-sweep's
+# zsum2 + zcarry2 + zsolve2; None where no capture matches the current
+# kernels.
+TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.860096e6 + 0.136960e6,
+           ("zsweep", "fp32", 2048, 4096): (34.207232e6 + 0.482304e6) + (2.129920e6 + 0.0) + (69.806848e6 + 0.815616e6)}
 
 
 def _peaks():
