@@ -134,6 +134,19 @@ def test_paper_grid_and_annulus(precision):
     assert _rel(Tg, To) <= TOL[precision]
 
 
+def test_column_tiles_with_thin_layers():
+    """FP32 z-sweep on column tiles of one class each, with layers of 3 and 2
+    columns: 4096 columns in layers of 2001, 3, 2 and 2090 give 35 tiles of at
+    most 128 columns (32 plain warps of 128 would straddle the interfaces), so
+    tiles start inside a lane's 16-byte segment, one lane reads three classes
+    and tiles of 3 and 2 columns store only their own columns."""
+    p = H.layered_annulus([1.0, 2.0, 2.003, 2.005, 4.0], [2001, 3, 2, 2090], [1.0, 20.0, 0.3, 5.0],
+                          100.0, 0.0, Nz=24)
+    T0 = H.random_field(p, seed=3)
+    Tg, To = _run_pair(p, 10, "fp32", T0=T0, factor=5.0)
+    assert _rel(Tg, To) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("face_mean", [H.FACE_ARITH])
 def test_arithmetic_face_mean(face_mean):
     p = H.config1().copy(face_mean=face_mean)
