@@ -1488,9 +1488,16 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     cudaError_t e = allow_smem(a.fn, a.smem);
     if (e != cudaSuccess) return e;
     if (maxNch > ZSEG2 * ZMAXM) return cudaErrorInvalidValue;
-    b.fn = (const void *)zcarry2_kernel<real>;
+    // carry pass: the fewest segments (warps per block) that cover the chunks
+    // -- a 1024-thread block of 32 segments holds a whole SM's registers, so a
+    // batch of short columns would run its column groups one block per SM,
+    // and in FP64 it spills
+    const int seg = maxNch <= 4 * ZMAXM ? 4 : maxNch <= 16 * ZMAXM ? 16 : ZSEG2;
+    b.fn = seg == 4    ? (const void *)zcarry2_kernel<real, 4>
+           : seg == 16 ? (const void *)zcarry2_kernel<real, 16>
+                       : (const void *)zcarry2_kernel<real, ZSEG2>;
     b.grid = dim3((maxNr + 31) / 32, n, 1);
-    b.block = dim3(32 * ZSEG2, 1, 1);
+    b.block = dim3(32 * seg, 1, 1);
     b.smem = 0;
     b.flip = false;
     int wpb = tu.zwpb;

@@ -744,16 +744,17 @@ __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__r
     }
 }
 
-// Pass 2: chunk carries.  A block of ZSEG2 warps serves 32 columns (lane =
-// column: every access is coalesced); warp s owns chunks [s m, (s+1) m),
-// m = ceil(nch / ZSEG2) <= ZMAXM, loads all their summaries and constants at
+// Pass 2: chunk carries.  A block of SEG warps (segments: 4, 16 or 32, the
+// fewest that cover the chunks) serves 32 columns (lane = column: every
+// access is coalesced); warp s owns chunks [s m, (s+1) m),
+// m = ceil(nch / SEG) <= ZMAXM, loads all their summaries and constants at
 // once, composes its segment's affine maps, joins the segments through shared
 // memory and writes cin_c = D_{c-1} and xin_c = X_{c+1} to zc[(c*2 + 0|1)*Nr + i].
-constexpr int ZSEG2 = 32;
+constexpr int ZSEG2 = 32;  // segments (warps per block) for up to ZSEG2 ZMAXM chunks
 constexpr int ZMAXM = 8;
 
-template <typename real>
-__global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<real> *__restrict__ args)
+template <typename real, int SEG>
+__global__ void __launch_bounds__(32 * SEG) zcarry2_kernel(const SweepArgs<real> *__restrict__ args)
 {
     pdl_launch_dependents();
     pdl_wait();
@@ -762,12 +763,12 @@ __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<rea
     if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
     const real *__restrict__ zs = A.zs;
     real *__restrict__ zc = A.zc;
-    __shared__ real sF[ZSEG2][33], sB[ZSEG2][33];
+    __shared__ real sF[SEG][33], sB[SEG][33];
     const int lane = threadIdx.x & 31, sgm = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     const bool col = i < Nr;
     const real *__restrict__ chb = A.chk + (size_t)(col ? A.colcls[i] : 0) * nch * 4;
-    const int m = (nch + ZSEG2 - 1) / ZSEG2;
+    const int m = (nch + SEG - 1) / SEG;
     const int c0 = sgm * m;
     const size_t st = (size_t)2 * Nr;
     real Bv[ZMAXM], Gv[ZMAXM], Fv[ZMAXM], Hv[ZMAXM], GPv[ZMAXM];
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(32 * ZSEG2) zcarry2_kernel(const SweepArgs<rea
     sB[sgm][lane] = Gm;
     __syncthreads();
     real X = real(0);
-    for (int v = ZSEG2 - 1; v > sgm; --v) X = fmad(sF[v][lane], X, sB[v][lane]);
+    for (int v = SEG - 1; v > sgm; --v) X = fmad(sF[v][lane], X, sB[v][lane]);
 #pragma unroll
     for (int u = ZMAXM - 1; u >= 0; --u) {
         if (col && u < m && c0 + u < nch) zc[(c0 + u) * st + Nr + i] = X;
