@@ -10,6 +10,7 @@
 // and heat_batch_step replays CUDA graphs of whole steps captured on the
 // batch's own stream, so host launch cost does not grow with n or with the
 // number of steps.  No block waits on another block.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -22,6 +23,7 @@
 namespace heat {
 size_t args_bytes(int precision);
 void fill_args(const heat_ctx *ctx, void *dst);
+void set_zitems(int precision, void *h, int n, const void *items, int n_items);
 cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPlan &plan);
 cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s);
 int ctx_set_dt(heat_ctx *ctx, double dt);
@@ -54,6 +56,8 @@ struct heat_batch {
     void *d_args = nullptr;
     SweepPlan plan;
     cudaGraphExec_t g1 = nullptr, gk = nullptr;
+    int4 *d_zitem = nullptr;  // work list of the lean z passes (see build_zitems)
+    int n_zitem = 0;
 };
 
 namespace {
@@ -74,6 +78,7 @@ void free_batch(heat_batch *b)
         heat_destroy(c);
     }
     if (b->d_args) cudaFree(b->d_args);
+    if (b->d_zitem) cudaFree(b->d_zitem);
     if (b->ev) cudaEventDestroy(b->ev);
     if (b->s) cudaStreamDestroy(b->s);
     delete b;
@@ -94,6 +99,40 @@ cudaError_t capture(heat_batch *b, int steps, cudaGraphExec_t *exec)
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// The work list of the lean z passes: one warp per (member, chunk, column
+// tile), the member's column tiles of one class each where z_tiles gives
+// them (FP32), else its warps of 32 V columns.  With it, no warp of a z pass
+// is idle: a grid over (widest member's warps, most chunks, members) leaves
+// the warps and chunks the smaller members lack empty.
+cudaError_t build_zitems(heat_batch *b)
+{
+    b->n_zitem = 0;
+    if (b->n > 0xffff) return cudaSuccess;  // (the grid then serves)
+    const int V = b->precision == HEAT_FP64 ? 2 : 4, COLS = 32 * V;
+    std::vector<int> it;
+    for (int i = 0; i < b->n; ++i) {
+        const heat_ctx *c = b->m[i];
+        const int Nr = c->g.Nr, nch = c->zp.n_chunks;
+        std::vector<int> t;
+        if (b->precision == HEAT_FP32) t = z_tiles(c->g.colcls, Nr, 4);
+        if (t.empty())
+            for (int g = 0; g * COLS < Nr; ++g) {
+                t.push_back(g * COLS), t.push_back(g * COLS), t.push_back(std::min(Nr, (g + 1) * COLS));
+                t.push_back(0);
+            }
+        for (int ch = 0; ch < nch; ++ch)
+            for (size_t k = 0; k < t.size(); k += 4) {
+                it.push_back(i | ch << 16), it.push_back(t[k]), it.push_back(t[k + 1]), it.push_back(t[k + 2]);
+            }
+    }
+    if (b->d_zitem) cudaFree(b->d_zitem), b->d_zitem = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_zitem, it.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_zitem, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e == cudaSuccess) b->n_zitem = (int)it.size() / 4;
     return e;
 }
 
@@ -161,7 +200,9 @@ int heat_batch_create(int n, const heat_geometry *geoms, const heat_materials *m
         b->m.push_back(c);
         fill_args(c, b->h_args.data() + ab * i);
     }
-    if ((e = cudaMalloc(&b->d_args, b->h_args.size())) != cudaSuccess ||
+    if ((e = build_zitems(b)) == cudaSuccess)
+        set_zitems(b->precision, b->h_args.data(), b->n, b->d_zitem, b->n_zitem);
+    if (e != cudaSuccess || (e = cudaMalloc(&b->d_args, b->h_args.size())) != cudaSuccess ||
         (e = apply_tuning(b, Tuning())) != cudaSuccess) {
         free_batch(b);
         return cuda_status(e);
@@ -183,6 +224,7 @@ int heat_batch_set_dt(heat_batch *b, const double *dts)
         if (st != HEAT_OK) return st;
         fill_args(b->m[i], b->h_args.data() + ab * i);  // table pointers may have moved
     }
+    set_zitems(b->precision, b->h_args.data(), b->n, b->d_zitem, b->n_zitem);
     return cuda_status(apply_tuning(b, b->plan.used));
 }
 

@@ -120,6 +120,11 @@ struct SweepArgs {
     const int *ucls;
     const int4 *ztile;        // z-sweep column tiles {wb, lo, hi, 0} (n_ztile of them; 0: warps of 32 V columns)
     int n_ztile;
+    // batch work list of the lean z passes, the same in every instance's
+    // arguments: {instance | chunk << 16, wb, lo, hi} per warp (n_zitem of
+    // them; 0: grid (column warps, chunks, instances))
+    const int4 *zitem;
+    int n_zitem;
     real *zs, *zc, *rho;
     real *f0, *f1;
 };

@@ -1480,8 +1480,16 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     // one warp per block for a (single) tiled instance: its tiles x chunks
     // then still fit in one wave of 16 resident warps per SM
     const int SWPB = tiled ? 1 : 4;
-    a.fn = lean ? (const void *)zsum2_kernel<real, V, lean ? MODE : MODE_DELTA> : (const void *)zsum_kernel<real, V, MODE>;
-    a.grid = dim3((groups + SWPB - 1) / SWPB, maxNch, n);
+    // a batch with a work list: one warp per (instance, chunk, column tile)
+    const int nitem = lean ? h[0].n_zitem : 0;
+    auto lean_grid = [&](int wpb) {
+        return nitem > 0 ? dim3((nitem + wpb - 1) / wpb, 1, 1) : dim3((groups + wpb - 1) / wpb, maxNch, n);
+    };
+    constexpr int LM = lean ? MODE : MODE_DELTA;
+    a.fn = !lean      ? (const void *)zsum_kernel<real, V, MODE>
+           : nitem > 0 ? (const void *)zsum2_kernel<real, V, LM, true>
+                       : (const void *)zsum2_kernel<real, V, LM, false>;
+    a.grid = lean ? lean_grid(SWPB) : dim3((groups + SWPB - 1) / SWPB, maxNch, n);
     a.block = dim3(32 * SWPB, 1, 1);
     a.smem = (size_t)SWPB * maxRc * 8 * sizeof(real);
     a.flip = true;
@@ -1506,9 +1514,10 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     // the lean solve keeps no forward results: 4 warps per block (as the
     // summary pass: 1 for a single tiled instance), staged (P, cp) rows only
     const int cw = lean ? SWPB : wpb;
-    c.fn = lean ? (const void *)zsolve2_kernel<real, V, lean ? MODE : MODE_DELTA>
-                : (const void *)zsolve_kernel<real, V, MODE>;
-    c.grid = dim3((groups + cw - 1) / cw, maxNch, n);
+    c.fn = !lean      ? (const void *)zsolve_kernel<real, V, MODE>
+           : nitem > 0 ? (const void *)zsolve2_kernel<real, V, LM, true>
+                       : (const void *)zsolve2_kernel<real, V, LM, false>;
+    c.grid = lean ? lean_grid(cw) : dim3((groups + cw - 1) / cw, maxNch, n);
     c.block = dim3(32 * cw, 1, 1);
     c.smem = lean ? (size_t)cw * ZNC * maxRc * 2 * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
     c.flip = true;

@@ -125,6 +125,21 @@ cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int fli
     return cudaSuccess;
 }
 
+// Point every instance's arguments (n of them in h, of the given precision)
+// at the batch work list of the lean z passes.
+void set_zitems(int precision, void *h, int n, const void *items, int n_items)
+{
+    for (int i = 0; i < n; ++i) {
+        if (precision == HEAT_FP64) {
+            SweepArgs<double> &a = static_cast<SweepArgs<double> *>(h)[i];
+            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items;
+        } else {
+            SweepArgs<float> &a = static_cast<SweepArgs<float> *>(h)[i];
+            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items;
+        }
+    }
+}
+
 // (Re)build the single-instance plan of a context and upload its arguments.
 cudaError_t ctx_plan(heat_ctx *ctx)
 {

@@ -133,6 +133,24 @@ __device__ __forceinline__ bool zl_tile(const SweepArgs<real> &A, int grp, int &
     lo = wb, hi = min(A.Nr, wb + 32 * V);
     return wb < A.Nr;
 }
+// The work of warp grp: instance mi, chunk c and column tile (wb, lo, hi),
+// from the batch work list (ITEMS), else from the grid (chunk = blockIdx.y,
+// instance = blockIdx.z); false when the warp has none.
+template <typename real, int V, bool ITEMS>
+__device__ __forceinline__ bool zl_work(const SweepArgs<real> *args, int grp, int &mi, int &c, int &wb, int &lo,
+                                        int &hi)
+{
+    if constexpr (ITEMS) {
+        if (grp >= args[0].n_zitem) return false;
+        const int4 it = args[0].zitem[grp];
+        mi = it.x & 0xffff, c = it.x >> 16, wb = it.y, lo = it.z, hi = it.w;
+        return true;
+    } else {
+        mi = blockIdx.z, c = blockIdx.y;
+        if (c >= args[mi].nch) return false;
+        return zl_tile<real, V>(args[mi], grp, wb, lo, hi);
+    }
+}
 // bits q of the lane's columns ib + q inside [lo, hi)
 template <int V>
 __device__ __forceinline__ unsigned zl_mask(int ib, int lo, int hi)
@@ -457,20 +475,18 @@ struct ZWalk {
 // results d0_j (the forward recurrence with a zero carry-in) are stored in the
 // output field buffer -- during the z-sweep it holds the superseded field --
 // and the chunk's carry summaries B = d0 at its last row and G0 = sum r wG go
-// to zs[(c*2 + s)*Nr + i].  Grid (column groups / warps per block, chunks,
-// instances).
-template <typename real, int V, int MODE>
+// to zs[(c*2 + s)*Nr + i].  Grid (column warps / warps per block, chunks,
+// instances), or with ITEMS (batch work list / warps per block).
+template <typename real, int V, int MODE, bool ITEMS>
 __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
-    const SweepArgs<real> &A = args[blockIdx.z];
-    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
-    if ((int)blockIdx.y >= A.nch) return;
     const int lane = threadIdx.x & 31;
     const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int wb, lo, hi;
-    if (!zl_tile<real, V>(A, grp, wb, lo, hi)) return;  // no column tile (warp-uniform)
-    const int c = blockIdx.y;
+    int mi, c, wb, lo, hi;
+    if (!zl_work<real, V, ITEMS>(args, grp, mi, c, wb, lo, hi)) return;  // no work (warp-uniform)
+    const SweepArgs<real> &A = args[mi];
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
     real *__restrict__ d0out = flip ? A.f0 : A.f1;
     ZWalk<real, V, MODE> W;
@@ -525,21 +541,19 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
 //   x_j  = d'_j + cp_j x_{j+1},
 // and the new field is theta + x (increment form) or x (literal form).  Rows
 // of d0 and theta are fetched ZQ at a time, double-buffered.
-template <typename real, int V, int MODE>
+template <typename real, int V, int MODE, bool ITEMS>
 __global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
-    const SweepArgs<real> &A = args[blockIdx.z];
-    const real *__restrict__ th = flip ? A.f1 : A.f0;
-    real *__restrict__ out = flip ? A.f0 : A.f1;  // holds d0 on entry
-    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
-    if ((int)blockIdx.y >= A.nch) return;
     constexpr bool LIT = MODE == MODE_LIT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int grp = blockIdx.x * (blockDim.x >> 5) + w;
-    int wb, lo, hi;
-    if (!zl_tile<real, V>(A, grp, wb, lo, hi)) return;  // no column tile (warp-uniform)
-    const int c = blockIdx.y;
+    int mi, c, wb, lo, hi;
+    if (!zl_work<real, V, ITEMS>(args, grp, mi, c, wb, lo, hi)) return;  // no work (warp-uniform)
+    const SweepArgs<real> &A = args[mi];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    real *__restrict__ out = flip ? A.f0 : A.f1;  // holds d0 on entry
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
     const int ib = wb + lane * V;
     // any: columns inside the field (read); smask: the tile's (stored)
