@@ -44,8 +44,8 @@ ELEM = {"fp64": 8, "fp32": 4}
 # (--set full, one step's launches): the r-sweep kernel, and the z-sweep's
 # zsum2 + zcarry2 + zsolve2; None where no capture matches the current
 # kernels.
-TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.860096e6 + 0.136960e6,
-           ("zsweep", "fp32", 2048, 4096): (34.207232e6 + 0.482304e6) + (2.129920e6 + 0.0) + (69.806848e6 + 0.815616e6)}
+TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.859328e6 + 0.183040e6,
+           ("zsweep", "fp32", 2048, 4096): (34.208000e6 + 0.530688e6) + (2.126080e6 + 0.0) + (69.806592e6 + 0.811008e6)}
 
 
 def _peaks():
