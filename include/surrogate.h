@@ -91,7 +91,7 @@ int surr_loss_grad(surr_ctx *s, const double *params, int B, const float *T_true
  * gradient; then the BF16 working copies are refreshed. */
 int surr_adam(surr_ctx *s, double lr, double beta1, double beta2, double eps);
 
-/* Inference with the solver as judge and fallback: run the network on B
+/* Inference checked against the solver, with fallback: run the network on B
  * samples; run the solver (FP32 batched path, the same dt and steps) on
  * n_check of them (indices (seed + i B / n_check) mod B); if any has
  * max|T_net - T_solver| > tol * max|T_solver - T_init|, run the solver on

@@ -25,7 +25,7 @@
  *   - Sec. 3 (last paragraph of the iteration part): each implicit system is a
  *     set of independent tridiagonal line systems solved by the Thomas method.
  *
- * Readings where the paper is silent or garbled (also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Boundary spacings: a mirror ghost cell beyond each outer face, so
  *     h_0 = 2 (r_0 - r_lo), h_N = 2 (r_hi - r_{N-1}), r_{-1/2} = r_lo and
  *     r_{N-1/2} = r_hi (zero at the axis), the same in z.
