@@ -92,6 +92,24 @@ def test_every_schedule_gives_the_same_answer(tuning):
     b.close()
 
 
+def test_work_list_mixes_tiled_and_plain_members():
+    """The batch's z passes run on a work list of (member, chunk, column tile):
+    the five-region cell at 512 and 1000 columns is tiled by column class,
+    the homogeneous cylinder and the small member are not; members of
+    different chunk counts (Nz 130 .. 1024) share one launch."""
+    from paper_1912_03744_gb300 import HeatBatch
+    probs = [H.config2(512, 256), H.config2(1000, 130), ENSEMBLE[0],
+             H.homogeneous_cylinder(300, 1024, R=2.0, Z=3.0, k=5.0, C=2.0e6, bc=(0, 1, 0, 1),
+                                    T_bc=(0, 250.0, 0, 310.0), T_init=300.0, q=1e5)]
+    ref, dts = _oracle_runs(probs, 9)
+    for precision in ("fp32", "fp64"):
+        b = HeatBatch(probs, dts, precision=precision)
+        b.step(9)
+        for m, To in zip(b.members, ref):
+            assert _rel(m.field(), To) <= TOL[precision], (precision, m.Nr, m.Nz)
+        b.close()
+
+
 def test_tune_leaves_the_state_unchanged_and_then_steps_correctly():
     from paper_1912_03744_gb300 import HeatBatch
     sel = _pick(ENSEMBLE, 4, seed=3)

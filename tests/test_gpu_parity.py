@@ -112,7 +112,12 @@ def test_ragged_and_long_lines_fp64(shape):
     assert _rel(Tg, To) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(31, 33), (4097, 5), (9000, 2), (3, 4097)])
+# FP32 shapes around the kernel choices: lines that fill their threads
+# exactly (2048, 64) or not (2047, 100), one past the register-resident
+# r-sweep (2049), ragged and partial z chunks (Nz 33, 40, 65; 8200 gives
+# 36-row chunks, not a multiple of the fetch groups)
+@pytest.mark.parametrize("shape", [(31, 33), (4097, 5), (9000, 2), (3, 4097), (2048, 40), (2047, 33),
+                                   (2049, 9), (64, 65), (100, 40), (8, 8200)])
 def test_ragged_fp32(shape):
     Nr, Nz = shape
     p = H.homogeneous_cylinder(Nr, Nz, R=2.0, Z=3.0, k=5.0, C=2.0e6,
