@@ -110,13 +110,21 @@ def _dist():
 
 
 def _reduce_max(x, ws):
+    """The maximum of x over the ranks (the replicas' slowest time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _whole_job(units_per_rank, ws, max_seconds):
+    """Whole-job throughput of ws replicas that each processed units_per_rank
+    units, over the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank / max_seconds
 
 
 def _barrier(ws):
@@ -477,7 +485,7 @@ def main():
         return
 
     peak, peak_kind = _peaks()
-    value = ws * act * args.steps / (tot_ms * 1e-3)
+    value = _whole_job(act * args.steps, ws, tot_ms * 1e-3)
 
     def roof(t, precision):
         """The dominant kernel is the r-sweep, one launch per step (the longest
@@ -511,7 +519,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof(main_t, args.precision),
         "cpu_baseline": cpu,
-        "e2e": {"value": ws * act * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": _whole_job(act * args.steps, ws, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": e2e_bytes / args.steps, "d2h_bytes_per_step": e2e_bytes / args.steps},
         "gpu_launches": main_t["launches"],
         "clocks": clk.summary(),
