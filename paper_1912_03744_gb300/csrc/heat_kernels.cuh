@@ -1477,9 +1477,14 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     for (int m = 0; m < n && lean; ++m)
         if (h[m].n_ztile > 0) tiled = true, groups = h[m].n_ztile > groups ? h[m].n_ztile : groups;
     Launch a, b, c;
-    // one warp per block for a (single) tiled instance: its tiles x chunks
-    // then still fit in one wave of 16 resident warps per SM
-    const int SWPB = tiled ? 1 : 4;
+    // warps per block: the most of 4, 2, 1 whose grid still runs as one wave
+    // of 16 resident warps per SM (the passes' register use), as every chunk
+    // walk then runs at once (config 2 tiled: 17 tiles x 128 chunks in blocks
+    // of 2; 4 would leave part of a second wave)
+    int SWPB = 4;
+    if (tiled)
+        while (SWPB > 1 && (long long)((groups + SWPB - 1) / SWPB) * maxNch * n > (long long)kSMs * 16 / SWPB)
+            SWPB /= 2;
     // a batch with a work list: one warp per (instance, chunk, column tile)
     const int nitem = lean ? h[0].n_zitem : 0;
     auto lean_grid = [&](int wpb) {
