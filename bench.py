@@ -44,8 +44,8 @@ ELEM = {"fp64": 8, "fp32": 4}
 # (--set full, one step's launches): the r-sweep kernel, and the z-sweep's
 # zsum2 + zcarry2 + zsolve2; None where no capture matches the current
 # kernels.
-TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.859328e6 + 0.183040e6,
-           ("zsweep", "fp32", 2048, 4096): (34.208000e6 + 0.530688e6) + (2.126080e6 + 0.0) + (69.806592e6 + 0.811008e6)}
+TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.859584e6 + 0.156160e6,
+           ("zsweep", "fp32", 2048, 4096): (34.207488e6 + 0.540160e6) + (2.126592e6 + 0.0) + (69.807872e6 + 0.954624e6)}
 
 
 def _peaks():
@@ -61,7 +61,7 @@ class Clocks:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, index):
         self.index = index
@@ -69,15 +69,20 @@ class Clocks:
 
     def __enter__(self):
         try:
+            # every 20 ms (the headline's timed region lasts a fraction of a
+            # second), started before the region so that it samples within it
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
         except OSError:
             self.p = None
+        self.t0 = time.time()  # samples count from here to __exit__
         return self
 
     def __exit__(self, *a):
         self.rows = []
+        t1 = time.time()
         if self.p is None:
             return
         self.p.terminate()
@@ -86,9 +91,16 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
+        import datetime
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
+            if len(f) < 10:
+                continue
+            try:
+                t = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                t = None
+            if t is None or self.t0 <= t <= t1:
                 self.rows.append(f)
 
     def summary(self):
