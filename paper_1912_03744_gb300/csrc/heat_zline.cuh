@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
 // and the new field is theta + x (increment form) or x (literal form).  Rows
 // of d0 and theta are fetched ZQ at a time, double-buffered.
 template <typename real, int V, int MODE, bool ITEMS>
-__global__ void __launch_bounds__(128) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
+__global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
     constexpr bool LIT = MODE == MODE_LIT;
