@@ -125,6 +125,8 @@ struct SweepArgs {
     // them; 0: grid (column warps, chunks, instances))
     const int4 *zitem;
     int n_zitem;
+    int zrc_max;              // with a work list: the most chunk rows of any instance (the
+                              // stride of a warp's shared-memory slice: a block mixes instances)
     real *zs, *zc, *rho;
     real *f0, *f1;
 };

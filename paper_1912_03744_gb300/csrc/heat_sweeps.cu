@@ -129,13 +129,19 @@ cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int fli
 // at the batch work list of the lean z passes.
 void set_zitems(int precision, void *h, int n, const void *items, int n_items)
 {
+    int rc_max = 0;
+    for (int i = 0; i < n; ++i) {
+        const int rc = precision == HEAT_FP64 ? static_cast<SweepArgs<double> *>(h)[i].Rc
+                                              : static_cast<SweepArgs<float> *>(h)[i].Rc;
+        rc_max = rc > rc_max ? rc : rc_max;
+    }
     for (int i = 0; i < n; ++i) {
         if (precision == HEAT_FP64) {
             SweepArgs<double> &a = static_cast<SweepArgs<double> *>(h)[i];
-            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items;
+            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items, a.zrc_max = rc_max;
         } else {
             SweepArgs<float> &a = static_cast<SweepArgs<float> *>(h)[i];
-            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items;
+            a.zitem = static_cast<const int4 *>(items), a.n_zitem = n_items, a.zrc_max = rc_max;
         }
     }
 }

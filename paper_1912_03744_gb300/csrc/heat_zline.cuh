@@ -520,7 +520,10 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
     real *dst = d0out + (size_t)j0 * Nr + W.ib;
     extern __shared__ __align__(16) unsigned char zs_smem[];
     if (W.warp_uniform()) {
-        W.stage(reinterpret_cast<real *>(zs_smem) + (size_t)(threadIdx.x >> 5) * Rc * 8);
+        // (a work list's block may hold warps of instances with different Rc:
+        // slices at the batch's largest)
+        const int Rs = ITEMS ? args[0].zrc_max : Rc;
+        W.stage(reinterpret_cast<real *>(zs_smem) + (size_t)(threadIdx.x >> 5) * Rs * 8);
         pdl_wait();
         if (full)
             W.template walk_full<1>(ucls, A.R, dst, emit_full);
@@ -585,7 +588,8 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
     int slot[ZNC], ns;
     const bool few = zl_classes(b, smask, slot, ns);
     extern __shared__ __align__(16) unsigned char zl_smem[];
-    real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * ZNC * Rc * 2;
+    const int Rs = ITEMS ? args[0].zrc_max : Rc;  // slice stride (see zsum2)
+    real *stg = reinterpret_cast<real *>(zl_smem) + (size_t)w * ZNC * Rs * 2;
     int off[V];
     if (few) {
         for (int u = lane; u < ns * (j1 - j0); u += 32) {

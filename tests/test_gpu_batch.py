@@ -110,6 +110,34 @@ def test_work_list_mixes_tiled_and_plain_members():
         b.close()
 
 
+def test_work_list_with_different_chunk_rows():
+    """Members whose z chunks differ in rows (Nz 20: one chunk of 20 rows;
+    300: chunks of 32; 9000: chunks of 36) share the work list's blocks, so
+    warps of different members stage their tables side by side in a block's
+    shared memory."""
+    from paper_1912_03744_gb300 import HeatBatch
+    cyl = dict(R=2.0, Z=3.0, k=5.0, C=2.0e6, bc=(0, 1, 0, 1), T_bc=(0, 250.0, 0, 310.0), T_init=300.0, q=1e5)
+    probs = [H.homogeneous_cylinder(100, 20, **cyl), H.homogeneous_cylinder(300, 300, **cyl),
+             H.homogeneous_cylinder(64, 9000, **cyl), H.homogeneous_cylinder(36, 20, **cyl)]
+    T0 = [H.random_field(p, seed=i, amp=20.0) for i, p in enumerate(probs)]
+    ref, dts = [], []
+    for p, t in zip(probs, T0):
+        o = Oracle(p)
+        tau = 5.0 * o.tau_exp()
+        o.set_field(t)
+        o.step(tau, 6)
+        ref.append(o.field())
+        dts.append(tau)
+    for precision in ("fp32", "fp64"):
+        b = HeatBatch(probs, dts, precision=precision)
+        for m, t in zip(b.members, T0):
+            m.set_field(t)
+        b.step(6)
+        for m, To in zip(b.members, ref):
+            assert _rel(m.field(), To) <= TOL[precision], (precision, m.Nr, m.Nz)
+        b.close()
+
+
 def test_tune_leaves_the_state_unchanged_and_then_steps_correctly():
     from paper_1912_03744_gb300 import HeatBatch
     sel = _pick(ENSEMBLE, 4, seed=3)
