@@ -2,7 +2,7 @@
 // Sec. 3, eq. "scheme_eq_2"; the line matrix is the axial operator of
 // eq. "Lambda_z" plus the mass term) in the literal and increment forms.
 //
-// Columns are strided, so lanes own columns: a warp owns 32 V adjacent
+// Columns are strided, so lanes own columns: a warp owns up to 32 V adjacent
 // columns (V per lane, one 16-byte segment of a row, so each row access of
 // the warp is one contiguous run) and one chunk of Rc rows, and every lane
 // walks its chunk row by row (interleaved Thomas).  The column partition and
@@ -13,11 +13,19 @@
 //   zcarry : the carry recurrences of every column over its chunks;
 //   zsolve : each chunk walked back from its carries, correcting every
 //            forward result by the carry-in times a prefix product of f.
-// Rows are fetched ZP at a time and double-buffered: the loads of the next
-// ZP rows (and of the warp's left / right halo columns) are in flight while
-// the current ZP rows are computed.  Table rows of the lane's column class
-// are read through the read-only cache; a lane whose V columns straddle two
-// classes (a layer interface) reads them per column.
+// A warp's columns are a column tile (zl_tile): 32 V columns from column 0,
+// or, where the instance has a tile table, the columns of one column class
+// (lanes start at the V-aligned column below the tile and store only its
+// columns), so that no warp straddles a layer interface.  A batch's warps
+// take their (instance, chunk, tile) from a work list (zl_work, ITEMS).
+// Rows are fetched ZQ at a time and double-buffered: the loads of the next
+// ZQ rows (and of the warp's left / right halo columns) are in flight while
+// the current ZQ rows are computed.  The chunk's table rows are staged in
+// shared memory before the walk (all loads in flight together): zsum stages
+// them for a warp of one column class, zsolve its (P, cp) rows for up to ZNC
+// classes; other warps read them per row and column through the read-only
+// cache.  Full chunks (a multiple of 2 ZQ rows, away from the z faces, one
+// row class) take lean walks with running row pointers.
 #pragma once
 
 #include <type_traits>
