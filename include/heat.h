@@ -160,10 +160,12 @@ int heat_energy(heat_ctx *ctx, double *E, double *Phi, double *Q);
  * callers that must not allocate at the point they ask for the heat balance
  * (a monitor under a hard device-memory budget, or one auditing a context
  * whose scratch it cannot assume idle).
- *   ctx: a live context; its device must be current.  Synchronizes ctx's stream.
+ *   ctx: a live context; its device must be current.  Synchronizes ctx's stream
+ *        (also when it returns an error after queueing work).
  *   E, Phi, Q: as heat_energy; any may be NULL.
  * Returns HEAT_ERR_TOO_LARGE if Nz > HEAT_NOALLOC_MAX_ROWS, HEAT_ERR_ARG for a
- * NULL ctx, HEAT_ERR_CUDA if a CUDA call fails, HEAT_ERR_NONFINITE as heat_energy.
+ * NULL ctx or when the current device is not ctx's, HEAT_ERR_CUDA if a CUDA
+ * call fails, HEAT_ERR_NONFINITE as heat_energy.
  * The first call on a device looks up the array's address
  * (cudaGetSymbolAddress) and must come before any stream capture on that
  * device.  The array keeps the last call's contents; a call rewrites every slot

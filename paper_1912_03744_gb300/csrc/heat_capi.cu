@@ -263,6 +263,13 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     ctx->precision = opt->precision;
     ctx->face_mean = opt->face_mean;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    {
+        const cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return cuda_status(e);
+        }
+    }
     // FP32 fields hold theta = T - T_init (precision where T varies little
     // around T_init); the FP64 field holds T itself, so a checkpoint through
     // heat_field / heat_set_field is lossless in every precision.

@@ -235,6 +235,7 @@ struct heat_ctx {
     int precision = HEAT_FP64;
     int face_mean = HEAT_HARMONIC;
     cudaStream_t stream = nullptr;
+    int device = -1;               // the device current at heat_create (owns every buffer)
     heat::Grid g;
     // problem constants
     double T_ref = 0.0;        // field stored as theta = T - T_ref

@@ -20,12 +20,18 @@
 // it.  That first call may load the module, so it must come before any
 // stream capture on that device.
 //
-// Contents persist between calls: each call overwrites the partial slots it
-// reads (rows 0..Nz-1) before reading them, and clears the result pair first,
-// so nothing from a previous call, possibly on a larger grid, can leak in.
-// Two calls whose device work overlapped would race on the one array; a
-// process-wide lock held until the call's stream has drained keeps calls made
-// through this entry point from overlapping.
+// Contents persist between calls: each call's row kernel overwrites the
+// partial slots it reads (rows 0..Nz-1) before the fold reads them, and the
+// fold writes both result slots, so nothing from a previous call, possibly on
+// a larger grid, can leak in.  Two calls whose device work overlapped would
+// race on the one array; a process-wide lock, held until the call's stream has
+// drained -- on the error paths too, once anything has been queued -- keeps
+// calls made through this entry point from overlapping.
+//
+// The array used is the one on the context's device: the call checks that
+// this device is current and otherwise returns HEAT_ERR_ARG (a launch with
+// another device current would fail, or with peer access reach the other
+// device's array).
 #include <cmath>
 #include <mutex>
 
@@ -53,6 +59,7 @@ extern "C" int heat_energy_noalloc(heat_ctx *ctx, double *E, double *Phi, double
     if (Nz > kNoAllocMaxRows) return HEAT_ERR_TOO_LARGE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return HEAT_ERR_CUDA;
+    if (dev != ctx->device) return HEAT_ERR_ARG;
 
     std::lock_guard<std::mutex> hold(g_noalloc_lock);
     if (!g_scratch_addr[dev]) {
@@ -63,7 +70,12 @@ extern "C" int heat_energy_noalloc(heat_ctx *ctx, double *E, double *Phi, double
     double *res = g_scratch_addr[dev];
     double *part = res + 2;
 
-    if (cudaMemsetAsync(res, 0, 2 * sizeof(double), ctx->stream) != cudaSuccess) return HEAT_ERR_CUDA;
+    // From the first enqueue on, every exit drains the stream before the lock
+    // is released, so no work of this call is left touching the array.
+    auto drained = [&](int status) {
+        cudaStreamSynchronize(ctx->stream);
+        return status;
+    };
     if (ctx->precision == HEAT_FP64)
         energy_kernel<double><<<Nz, 256, 0, ctx->stream>>>(static_cast<const double *>(ctx->d_field[ctx->cur]), Nr, Nz,
                                                           ctx->d_rowcls, ctx->d_colcls, ctx->dR.full, ctx->dZ.full,
@@ -72,12 +84,13 @@ extern "C" int heat_energy_noalloc(heat_ctx *ctx, double *E, double *Phi, double
         energy_kernel<float><<<Nz, 256, 0, ctx->stream>>>(static_cast<const float *>(ctx->d_field[ctx->cur]), Nr, Nz,
                                                          ctx->d_rowcls, ctx->d_colcls, ctx->dR.full, ctx->dZ.full,
                                                          ctx->d_wr, ctx->d_wz, part);
-    if (cudaGetLastError() != cudaSuccess) return HEAT_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return drained(HEAT_ERR_CUDA);
     energy_final_kernel<<<1, 256, 0, ctx->stream>>>(part, Nz, res);
-    if (cudaGetLastError() != cudaSuccess) return HEAT_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return drained(HEAT_ERR_CUDA);
 
     double out[2];
-    if (cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return HEAT_ERR_CUDA;
+    if (cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return drained(HEAT_ERR_CUDA);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return HEAT_ERR_CUDA;
     if (E) *E = out[0] + ctx->E_ref;
     if (Phi) *Phi = out[1];

@@ -37,6 +37,14 @@ MUTANTS = {
         "d[j] = w * Tb[c] + lambda_r(o, Tb, i, j) + o->Dzl[c] * o->Tbc[2] + o->Dzh[c] * o->Tbc[3];"),
     "energy_weight_cell_width": ("double wgt = o->rc[i] * o->hbar[i] * o->etabar[j];",
                                  "double wgt = o->rc[i] * o->dr[i] * o->etabar[j];"),
+    # the explicit limit (tau_exp): a dropped Dirichlet coupling, dropped z
+    # couplings, the half-step length taken for the step
+    "tau_exp_drops_dirichlet": ("o->Drl[c] + o->Drh[c] + o->Dzl[c] + o->Dzh[c];\n        if (s > 0.0",
+                                "o->Drl[c] + o->Drh[c] + o->Dzl[c];\n        if (s > 0.0"),
+    "tau_exp_drops_z_couplings": ("double s = o->Arm[c] + o->Arp[c] + o->Azm[c] + o->Azp[c] +",
+                                  "double s = o->Arm[c] + o->Arp[c] +"),
+    "tau_exp_half_step": ("if (s > 0.0 && o->cap[c] / s < best) best = o->cap[c] / s;",
+                          "if (s > 0.0 && o->cap[c] / s < best) best = 0.5 * o->cap[c] / s;"),
 }
 
 

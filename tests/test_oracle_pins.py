@@ -87,6 +87,70 @@ def test_two_cell_step_by_hand():
                                [Arp0, Arm1, D0, D1], rtol=1e-14)
 
 
+# ------------------------------------------------------------- C8 limit
+def test_explicit_limit_by_hand():
+    """tau_exp = min over active cells of C / (sum of the cell's couplings),
+    the forward-Euler positivity limit of the assembled operator (reading of
+    the workload's "50x the explicit stability limit"), worked by hand.
+
+    2x1 grid of ``_two_cell_problem``: cell 0 has Arp = 40/9 and the Dirichlet
+    coefficient 1, C = 1 -> 9/49; cell 1 has Arm = 50/63 and 5/2, C = 3 ->
+    378/415.  The limit is 9/49, set by the Dirichlet-coupled cell 0.
+    """
+    o = Oracle(_two_cell_problem())
+    assert abs(o.tau_exp() - 9.0 / 49.0) <= 1e-15
+
+
+def _void_corner_problem():
+    # 2x2 grid: r faces 0, 1, 3 (one cell each), z faces 0, 2, 4 (one cell
+    # each).  Region 0 (k 2, C 1) at the bottom left, region 2 (k 20, C 1)
+    # above it, region 1 (k 5, C 3) at the bottom right; the top right cell is
+    # in no box (void).  Dirichlet T = 10 on the top face z = 4.
+    return H.Problem(
+        name="hand2x2", r_faces=np.array([0.0, 1.0, 3.0]), r_cells=np.array([1, 1], np.int32),
+        z_faces=np.array([0.0, 2.0, 4.0]), z_cells=np.array([1, 1], np.int32),
+        boxes=np.array([[0.0, 1.0, 0.0, 2.0], [1.0, 3.0, 0.0, 2.0], [0.0, 1.0, 2.0, 4.0]]),
+        box_region=np.array([0, 1, 2], np.int32),
+        bc=np.array([0, 0, 0, 1], np.int32), T_bc=np.array([0.0, 0.0, 0.0, 10.0]),
+        k=np.array([2.0, 5.0, 20.0]), C=np.array([1.0, 3.0, 1.0]), q=np.zeros(3), T_init=0.0)
+
+
+def test_explicit_limit_with_void_and_dirichlet_by_hand():
+    """The limit on a grid with a void cell and a Dirichlet face, by hand.
+
+    z: centres 1, 3; eta = 2 everywhere (mirror ghosts), etabar = 2.
+    r: as the 2x1 case (Arp(0) = 40/9, Arm(1) = 50/63).
+    Bottom-left (k 2) to top-left (k 20) face: harmonic mean with half widths
+    1 and 1, 2 / (1/2 + 1/20) = 40/11; Azp = Azm = (40/11) / (2 * 2) = 10/11.
+    Cells (sum of couplings, C / sum):
+      (0,0): 40/9 + 10/11 = 530/99            -> 99/530 ~ 0.1868
+      (1,0): 50/63 (the void neighbour above adds nothing) -> 3 * 63/50 = 3.78
+      (0,1): Azm 10/11 + Dirichlet 2*20/(2*2) = 10 (the void neighbour to the
+             right adds nothing) = 120/11    -> 11/120 ~ 0.0917
+    The void cell is excluded.  Limit: 11/120, set by the Dirichlet face.
+    """
+    o = Oracle(_void_corner_problem())
+    assert (o.grid()["region"] == np.array([[0, 1], [2, -1]])).all()
+    c = o.coeffs()
+    np.testing.assert_allclose([c["Azp"][0, 0], c["Azm"][1, 0], c["Dzh"][1, 0], c["Arp"][1, 0]],
+                               [10.0 / 11.0, 10.0 / 11.0, 10.0, 0.0], rtol=1e-14)
+    assert abs(o.tau_exp() - 11.0 / 120.0) <= 1e-15
+
+
+@pytest.mark.parametrize("top", [H.BC_NEUMANN, H.BC_DIRICHLET])
+def test_explicit_limit_of_a_uniform_column_is_textbook(top):
+    """One radial cell, N uniform axial cells of height dz, conductivity k,
+    capacity C: the interior cells give the textbook explicit limit of the 1D
+    heat equation, C dz^2 / (2k); a Dirichlet face at half a cell from the
+    last centre adds 2k/dz^2 there, giving C dz^2 / (3k)."""
+    k, C, Z, N = 3.0, 5.0, 2.0, 8
+    p = H.homogeneous_cylinder(1, N, R=1.0, Z=Z, k=k, C=C, bc=(0, 0, 0, top),
+                               T_bc=(0.0, 0.0, 0.0, 1.0), T_init=0.0, q=0.0)
+    dz = Z / N
+    want = C * dz * dz / ((3.0 if top == H.BC_DIRICHLET else 2.0) * k)
+    assert abs(Oracle(p).tau_exp() - want) <= 1e-14 * want
+
+
 # ------------------------------------------------------------------- I0
 def _assemble(o, T, tau, implicit):
     """Dense 2D system of one half-step from the oracle's per-cell couplings."""
