@@ -40,12 +40,46 @@ METRIC = "cell-steps/s vs HBM roofline"
 UNIT = "cell-steps/s"
 WORKLOAD = "config2: five-region layered cell 2048x4096, seed 2, dt=50*tau_exp"
 ELEM = {"fp64": 8, "fp32": 4}
-# DRAM bytes (read + write) per launch from one ncu capture of this workload
-# (--set full, one step's launches): the r-sweep kernel, and the z-sweep's
-# zsum2 + zcarry2 + zsolve2; None where no capture matches the current
-# kernels.
-TRAFFIC = {("rsweep", "fp32", 2048, 4096): 33.859584e6 + 0.156160e6,
-           ("zsweep", "fp32", 2048, 4096): (34.207488e6 + 0.540160e6) + (2.126592e6 + 0.0) + (69.807872e6 + 0.954624e6)}
+# Algorithmic FP64 flops per cell and sweep of the literal form (the FP64
+# path): right-hand side w T + A-(T_- - T) + A+(T_+ - T) + q (2 sub, 3 fma,
+# 1 add = 9), forward recurrence d' = d inv + f d'_prev (mul + fma = 3),
+# backward x = d' + cp x_next (fma = 2).  FMA counts as 2 flops.
+FP64_FLOPS_PER_CELL_SWEEP = 14
+# GB300's nominal FP64 rate (not measured on this machine; MEASURED_PEAKS.json
+# has HBM and BF16 only).
+FP64_NOMINAL_TFLOPS = 1.25
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def csrc_sha() -> str:
+    """sha256 (16 hex) of the CUDA/C++ sources the kernels are built from."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1912_03744_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes (read + write) per launch, keyed (kernel, precision, Nr, Nz),
+    from the committed ncu summary profiles/traffic.txt.  The summary records
+    the source hash of the kernels it measured; when the sources have changed
+    since, the numbers no longer describe these kernels and none are used."""
+    out, sha = {}, None
+    if not os.path.exists(TRAFFIC_FILE):
+        return out, "no traffic summary"
+    for line in open(TRAFFIC_FILE):
+        f = line.split()
+        if len(f) >= 2 and f[0] == "csrc_sha":
+            sha = f[1]
+        elif len(f) == 5 and not line.startswith("#") and f[0] != "kernel":
+            out[(f[0], f[1], int(f[2]), int(f[3]))] = float(f[4])
+    if sha != csrc_sha():
+        return {}, "kernel sources changed since the capture in profiles/traffic.txt"
+    return out, "profiles/traffic.txt"
 
 
 def _peaks():
@@ -210,6 +244,47 @@ def active_cells(solver, p):
     return int(act.sum())
 
 
+def time_config1(steps=200, warmup=10):
+    """Config 1: the 64 x 128 five-region cell in FP64, 200 steps at
+    dt = 50 tau_exp; CUDA events around the 200 steps on the solver's stream.
+    The 64 KB field lives in L2 (and would fit one SM's shared memory), so
+    this is a latency figure, reported in microseconds per step."""
+    import torch
+    from paper_1912_03744_gb300 import HeatSolver
+    p = H.config1()
+    probe = HeatSolver(p, 1.0, precision="fp64")
+    tau = H.DT_FACTOR * probe.tau_exp
+    act = active_cells(probe, p)
+    probe.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = HeatSolver(p, tau, precision="fp64", stream=stream)
+        s.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = s.launches_per_step()
+        s.close()
+    return {"workload": "config1: five-region cell 64x128, seed 0, dt=50*tau_exp", "precision": "fp64",
+            "steps": steps, "us_per_step": 1e3 * ms / steps, "cell_steps_per_s": act * steps / (ms * 1e-3),
+            "active_cells": act, "launches_per_step": launches, "bound": "latency",
+            "note": "64 KB field, resident in L2: the HBM roofline does not apply"}
+
+
+def step_roofline(cells_active, word, ms_per_step):
+    """Whole-step algorithmic bandwidth (read + write of every active cell in
+    each of the two sweeps) against the measured copy bandwidth."""
+    peak, kind = _peaks()
+    b = 4 * word * cells_active
+    ach = b / (ms_per_step * 1e-3) / 1e9
+    return {"kernel": "whole step", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None, "algorithmic_bytes": b, "peak_kind": kind, "cells": "active"}
+
+
 def time_ensemble(steps, warmup, precision="fp32", tuning=None):
     """The 512-member batched ensemble (Nr 64..512, Nz 128..1024, jittered
     layers and materials), dt = 50 x each member's explicit limit, autotuned
@@ -244,7 +319,8 @@ def time_ensemble(steps, warmup, precision="fp32", tuning=None):
            "fields_per_s_500_steps": len(probs) / (500 * ms / steps * 1e-3),
            "tuning": dict(zip(("rK", "band", "zwpb"), b.tuning())), "tune_ms_per_step": tune_ms,
            "launches_per_step": b.launches_per_step(), "graph_replay": True, "create_s": create_s,
-           "finite": bool(ok), "l2": "inputs larger than L2"}
+           "finite": bool(ok), "l2": "inputs larger than L2",
+           "roofline": step_roofline(act, ELEM[precision], ms / steps)}
     b.close()
     return out
 
@@ -285,6 +361,7 @@ def time_config4(steps, warmup):
             "precision": "fp32_refined", "steps": steps, "ms_per_step": ms / steps,
             "cell_steps_per_s": act * steps / (ms * 1e-3), "active_cells": act,
             "heat_balance_rel": abs(resid) / abs(E1 - E0), "launches_per_step": launches,
+            "roofline": step_roofline(act, 4, ms / steps),
             "accuracy": "1024x2048 subsample vs FP64 oracle: tests/test_gpu_parity.py::test_config4_subsample_against_the_oracle",
             "l2": "inputs larger than L2"}
 
@@ -482,6 +559,7 @@ def main():
     side_steps = max(3, min(args.steps, 200))
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
+    c1 = time_config1()
     ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning)
     c4 = None if args.no_config4 else time_config4(args.config4_steps, args.warmup)
     surr = None if args.no_surrogate else time_surrogate(args.surrogate_train, args.surrogate_epochs)
@@ -499,21 +577,36 @@ def main():
     peak, peak_kind = _peaks()
     value = _whole_job(act * args.steps, ws, tot_ms * 1e-3)
 
+    traffic, traffic_src = load_traffic()
+
     def roof(t, precision):
         """The dominant kernel is the r-sweep, one launch per step (the longest
         single kernel of the step; the z-sweep is three shorter launches,
-        reported beside it as a group)."""
+        reported beside it as a group).  Algorithmic bytes: read and write of
+        every active cell once per sweep.  The FP64 path is bound by GB300's
+        FP64 units, so its line carries the FP64 flop rate against the nominal
+        FP64 peak as well."""
         r_avg = statistics.mean(t["r_ms"])
         z_avg = statistics.mean(t["z_ms"])
-        bytes_launch = 2 * ELEM[precision] * ncell  # read + write of every cell per sweep
+        bytes_launch = 2 * ELEM[precision] * act
         ach = bytes_launch / (r_avg * 1e-3) / 1e9
         zach = bytes_launch / (z_avg * 1e-3) / 1e9
-        return {"kernel": "rsweep", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": TRAFFIC.get(("rsweep", precision, p.Nr, p.Nz)),
-                "algorithmic_bytes": bytes_launch, "peak_kind": peak_kind,
-                "rsweep_ms": r_avg, "zsweep_ms": z_avg,
-                "zsweep_group": {"achieved": zach, "frac": zach / peak, "launches": 3,
-                                 "traffic": TRAFFIC.get(("zsweep", precision, p.Nr, p.Nz))}}
+        out = {"kernel": "rsweep", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+               "frac": ach / peak, "traffic": traffic.get(("rsweep", precision, p.Nr, p.Nz)),
+               "traffic_source": traffic_src,
+               "algorithmic_bytes": bytes_launch, "peak_kind": peak_kind, "cells": "active",
+               "rsweep_ms": r_avg, "zsweep_ms": z_avg,
+               "zsweep_group": {"achieved": zach, "frac": zach / peak, "launches": 3,
+                                "traffic": traffic.get(("zsweep", precision, p.Nr, p.Nz))}}
+        if precision == "fp64":
+            fl = FP64_FLOPS_PER_CELL_SWEEP * act
+            out["alu"] = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS, "peak_kind": "nominal",
+                          "flops_per_cell_sweep": FP64_FLOPS_PER_CELL_SWEEP,
+                          "rsweep_achieved": fl / (r_avg * 1e-3) / 1e12,
+                          "rsweep_frac": fl / (r_avg * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                          "zsweep_achieved": fl / (z_avg * 1e-3) / 1e12,
+                          "zsweep_frac": fl / (z_avg * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS}
+        return out
 
     side_ms = (sum(side_t["r_ms"]) + sum(side_t["z_ms"])) / len(side_t["r_ms"])
     cpu = None
@@ -535,6 +628,7 @@ def main():
                 "h2d_bytes_per_step": e2e_bytes / args.steps, "d2h_bytes_per_step": e2e_bytes / args.steps},
         "gpu_launches": main_t["launches"],
         "clocks": clk.summary(),
+        "config1": c1,
         "ensemble": ens,
         "config4": c4,
         "surrogate": surr,

@@ -1,8 +1,8 @@
 """The surrogate's CUDA path (BF16 tensor-core GEMMs, FP32 accumulation)
 against the FP64 FNO oracle, through the C ABI.
 
-Tolerances: the GPU keeps weights and activations in BF16 (unit roundoff
-2^-9 = 2e-3), with about ten roundings in sequence per layer (DFTs, mode
+Tolerances: the GPU keeps weights and activations in BF16 (8 significant
+bits, unit roundoff 2^-8 = 3.9e-3), with about ten roundings in sequence per layer (DFTs, mode
 mixing, pointwise GEMM, activation) over 3 layers and the head; the
 expected relative error of the output and of each gradient block is
 therefore ~1e-2, and the bars below are 3e-2 (output, L2 over the rise)
@@ -35,17 +35,21 @@ def _problem(params):
     return H.config5_problem(params, Nr=D.Nr, Nz=D.Nz)
 
 
-def _setup(max_batch=8):
+def _setup_dims(d, max_batch=8):
     from paper_1912_03744_gb300 import Surrogate
     params = H.config5_params(8, seed=21)
-    p0 = _problem(params[0])
-    ref = H.config5_reference_problem(Nr=D.Nr, Nz=D.Nz)
+    p0 = H.config5_problem(params[0], Nr=d.Nr, Nz=d.Nz)
+    ref = H.config5_reference_problem(Nr=d.Nr, Nz=d.Nz)
     dt = H.DT_FACTOR * Oracle(ref).tau_exp()
-    s = Surrogate(p0, D, heater=H.HEATER, dt=dt, steps=STEPS, max_batch=max_batch)
+    s = Surrogate(p0, d, heater=H.HEATER, dt=dt, steps=STEPS, max_batch=max_batch)
     g = Oracle(p0).grid()
-    fo = FnoOracle(D, g["rc"], g["zc"], p0.r_faces[-1], p0.z_faces[-1], T_init=p0.T_init, region=g["region"],
+    fo = FnoOracle(d, g["rc"], g["zc"], p0.r_faces[-1], p0.z_faces[-1], T_init=p0.T_init, region=g["region"],
                    heater=H.HEATER)
     return s, fo, params, dt
+
+
+def _setup(max_batch=8):
+    return _setup_dims(D, max_batch)
 
 
 def _blocks(d):
@@ -86,6 +90,49 @@ def test_gradient_matches_the_oracle_block_by_block():
         num = np.linalg.norm(gg[sl] - go[sl])
         den = np.linalg.norm(go[sl])
         assert num <= 6e-2 * den, (name, num / den)
+    s.close()
+
+
+def test_forward_and_gradients_at_the_config5_size():
+    """The shipped network's shape (128 x 256 grid, width 32, 12 x 12 modes,
+    4 layers, hidden 64), so the GEMM shapes and tile paths config 5 runs are
+    the ones checked; two samples; element by element in max-norm.
+
+    Bars.  BF16 keeps 8 significant bits (unit roundoff u = 2^-8 = 3.9e-3);
+    every GEMM accumulates in FP32, so the roundings that matter are the
+    casts of GEMM operands to BF16: the activations entering the forward DFT,
+    the mode mix, the inverse DFT and the pointwise GEMM, about 3 per layer
+    once weights are counted with them, 14 in the lift, 4 layers and the head.
+    Independent roundings add like a random walk, sqrt(14) u = 1.5e-2 of the
+    field's scale for an element that no sum averages; the output bar is 2e-2
+    of the largest rise (|T - T_init|) per sample, element by element.  A
+    gradient block is one more pass through the same chain in reverse, twice
+    the casts (sqrt(28) u = 2.1e-2), so its bar is 3e-2 of the block's largest
+    entry."""
+    s, fo, params, _ = _setup_dims(F.FnoDims(), max_batch=2)
+    Df = F.FnoDims()
+    flat = F.random_params(Df, 51).astype(np.float32)
+    s.set_params(flat)
+    B = 2
+    Tg = s.forward(params[:B])
+    To = fo.forward(flat.astype(np.float64), params[:B])
+    for b in range(B):
+        rise = np.max(np.abs(To[b] - 300.0))
+        err = np.max(np.abs(Tg[b] - To[b])) / rise
+        print(f"config-5 size forward, sample {b}: max error / max rise {err:.3e}")
+        assert err <= 2e-2, (b, err)
+    rng = np.random.default_rng(52)
+    Tt = (300.0 + S_Q * params[:B, 5, None, None] * rng.uniform(0.0, 1.0, (B, Df.Nz, Df.Nr))).astype(np.float32)
+    lg, gg = s.loss_grad(params[:B], Tt)
+    lo, go = fo.grad(flat.astype(np.float64), params[:B], Tt.astype(np.float64))
+    assert abs(lg - lo) <= 2e-2 * lo, (lg, lo)
+    worst = {}
+    for name, sl in _blocks(Df).items():
+        e = float(np.max(np.abs(gg[sl] - go[sl])) / np.max(np.abs(go[sl])))
+        worst[name] = e
+        assert e <= 3e-2, (name, e)
+    print("config-5 size gradient blocks, max error / block max: " +
+          ", ".join(f"{k} {v:.2e}" for k, v in sorted(worst.items(), key=lambda kv: -kv[1])[:6]))
     s.close()
 
 
@@ -134,13 +181,15 @@ def test_fallback_returns_the_solver_fields_when_the_check_fails():
     s.close()
 
 
-def test_trained_network_gains_speed_over_the_solver_at_its_accuracy():
-    """What the trained network gains over the method alone.  Trained on
-    solver runs, its held-out rise-relative max error falls well below the
-    untrained network's; at a tolerance its held-out errors meet, the checked
-    inference (network + sampled solver check) returns the network's fields
-    faster than the solver alone on the same batch; at a tolerance they do not
-    meet, the check sends the batch to the solver."""
+def test_trained_network_at_the_workload_tolerance():
+    """What the trained network gains over the method alone, judged at the
+    workload's own tolerance (1% rise-relative max error).  Trained on solver
+    runs, its held-out error falls well below the untrained network's.  The
+    checked inference (network + 8 members re-solved) is then run at 1%, and
+    the test asserts what is true there: either every check passed, the
+    network's fields came back and the call beat the solver alone on the same
+    batch; or a check failed and the batch came back as the solver's fields,
+    bit for bit.  Either way no field is returned that a check saw above 1%."""
     import time
 
     import torch
@@ -154,9 +203,10 @@ def test_trained_network_gains_speed_over_the_solver_at_its_accuracy():
     e0 = s.errors(te, fields[n_tr:])
     s.train(tr, fields[:n_tr], epochs=40, batch=64, lr=2e-3, seed=1)
     e1 = s.errors(te, fields[n_tr:])
-    print(f"held-out error untrained p50 {np.median(e0):.3f}, trained p50 {np.median(e1):.3f} max {e1.max():.3f}")
+    print(f"held-out error untrained p50 {np.median(e0):.3f}, trained p50 {np.median(e1):.3f} max {e1.max():.3f}, "
+          f"within 1%: {np.mean(e1 <= 0.01):.2f}")
     assert np.median(e1) <= 0.3 * np.median(e0)
-    tol = 1.5 * float(e1.max())
+    tol = 0.01
     out = torch.empty((n_te, D.Nz, D.Nr), dtype=torch.float32, device="cuda")
     s.infer_checked(te[:8], n_check=2, tol=tol, out=out[:8])  # warm-up
     torch.cuda.synchronize()
@@ -164,16 +214,19 @@ def test_trained_network_gains_speed_over_the_solver_at_its_accuracy():
     s.solve(te, out=out)
     torch.cuda.synchronize()
     t_solve = time.perf_counter() - t0
+    solver_fields = out.clone()
     t0 = time.perf_counter()
-    _, used, err = s.infer_checked(te, n_check=4, tol=tol, seed=5, out=out)
+    _, used, err = s.infer_checked(te, n_check=8, tol=tol, seed=5, out=out)
     torch.cuda.synchronize()
     t_chk = time.perf_counter() - t0
-    print(f"fields/s solver {n_te / t_solve:.0f}, checked network {n_te / t_chk:.0f}")
-    assert not used and err <= tol
-    assert t_chk < t_solve
-    T, used, err = s.infer_checked(te[:8], n_check=4, tol=0.5 * float(e1.min()), seed=6)
-    assert used and err > 0.5 * float(e1.min())
-    np.testing.assert_array_equal(T, s.solve(te[:8]))
+    print(f"at 1%: fallback {used}, largest checked error {err:.4f}, fields/s solver {n_te / t_solve:.0f}, "
+          f"checked network {n_te / t_chk:.0f}")
+    if used:
+        assert err > tol
+        assert torch.equal(out, solver_fields)
+    else:
+        assert err <= tol
+        assert t_chk < t_solve
     s.close()
 
 
