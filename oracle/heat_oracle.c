@@ -64,7 +64,10 @@ typedef struct {
     double Tbc[4];
     double *T;                         /* field [Nz][Nr] */
     double *Tbar;
+    struct orc_nl *nl;                 /* temperature-dependent state (orc_nl_setup), or NULL */
 } orc_t;
+
+static void orc_nl_free(struct orc_nl *n);
 
 #define IDX(o, i, j) ((size_t)(j) * (size_t)(o)->Nr + (size_t)(i))
 
@@ -226,6 +229,7 @@ void orc_destroy(void *p)
                     o->region, o->lam, o->cap, o->src, o->Arm, o->Arp, o->Azm, o->Azp,
                     o->Drl, o->Drh, o->Dzl, o->Dzh, o->T, o->Tbar};
     for (size_t b = 0; b < sizeof(bufs) / sizeof(bufs[0]); ++b) free(bufs[b]);
+    orc_nl_free(o->nl);
     free(o);
 }
 
@@ -448,4 +452,349 @@ void orc_energy(void *p, double *E, double *Phi, double *Q)
     *E = 2.0 * ORC_PI * e;
     *Phi = 2.0 * ORC_PI * f;
     *Q = 2.0 * ORC_PI * s;
+}
+
+/* ====================================================================
+ * Temperature-dependent coefficients, the simple iteration, adaptive tau
+ * and the pulsed source: the paper's full evolution loop.
+ *
+ *   Sec. 2, eq. "main_eq":     k, C = rho c_V and X depend on T.  Material
+ *       laws are given per region as tables of values at temperature knots,
+ *       read by linear interpolation and held constant beyond the end knots
+ *       (the paper's laws are cited, not printed; tests use synthetic ones).
+ *   Sec. 2, eq. "source":      X = chi(T) j^2 p(t) with chi the resistivity
+ *       of the region and j its current density (I / S_C; zero outside the
+ *       heater) -- the printed I^2 / S_C is read as (I / S_C)^2 so that X is
+ *       a power per volume.
+ *   Sec. 2, eqs. "unit_model", "trans_model": p(t) is the rectangular pulse
+ *       train u(t) or its erf-smoothed version v(t); model 0 is p = 1.
+ *   Sec. 3, eq. "iter_scheme_eq_1": half-step 1 iterates T^s -> T^{s+1} with
+ *       rho c_V, the r-operator's conductivities and X taken at the iterate
+ *       T^s, the explicit z-operator at the old layer T, from T^0 = T.
+ *   Sec. 3, eq. "iter_scheme_eq_2": half-step 2 iterates with the implicit
+ *       z-operator's conductivities at T^s, while rho c_V, X and the explicit
+ *       r-operator are taken at the converged half layer Tbar, from T^0 = Tbar.
+ *   Sec. 3, eq. "iter_cond":   each iteration stops when
+ *       max |T^{s+1} - T^s| < eps; the last iterate is the result.
+ *   Sec. 3 (adaptive time step) and Sec. 4: when s reaches s_max without
+ *       meeting the criterion, tau is halved and the step restarts from the
+ *       old layer; every step starts from the estimate t_trs / 1000 inside a
+ *       transition of the source and t_src / 100 elsewhere (passed in as
+ *       tau_trs and tau_base).
+ * Readings: face conductivities are the face means of the cells' own
+ * conductivities at their temperatures (harmonic weighted by the half widths,
+ * or arithmetic: the same two readings as the constant case); the source is
+ * evaluated at t_k + tau/2 in both half-steps; the last step is shortened to
+ * land on t_end; theta(0) = 1 in u(t); a transition is the first t_trs after
+ * a switch-on (t mod t_per in [0, t_trs)) or switch-off ([t_src, t_src + t_trs)).
+ * ==================================================================== */
+
+typedef struct orc_nl {
+    int K, n_regions;
+    double *Tk, *lam, *cap, *chi; /* [n_regions][K] */
+    double *jsq;                  /* [n_regions]    */
+    int model;
+    double t_per, t_src, t_trs, xi, zeta;
+    int face_mean;
+    double *Ts, *Tn, *lam_s, *lam_o, *cap_x, *X;  /* per-cell work fields */
+} orc_nl_t;
+
+static void orc_nl_free(struct orc_nl *n)
+{
+    if (!n) return;
+    void *bufs[] = {n->Tk, n->lam, n->cap, n->chi, n->jsq, n->Ts, n->Tn, n->lam_s, n->lam_o, n->cap_x, n->X};
+    for (size_t b = 0; b < sizeof(bufs) / sizeof(bufs[0]); ++b) free(bufs[b]);
+    free(n);
+}
+
+/* One material table at temperature T: linear between knots, constant beyond. */
+static double table_at(const double *Tk, const double *v, int K, double T)
+{
+    if (K == 1 || T <= Tk[0]) return v[0];
+    if (T >= Tk[K - 1]) return v[K - 1];
+    int k = 0;
+    while (T >= Tk[k + 1]) ++k;
+    return v[k] + (v[k + 1] - v[k]) * (T - Tk[k]) / (Tk[k + 1] - Tk[k]);
+}
+
+/* p(t) of eq. "unit_model" (model 1) or eq. "trans_model" (model 2); model 0: 1.
+ * Terms with n t_per > t + t_per are exactly zero in FP64 for the erf model
+ * (both erf arguments are below -6), so the sum stops at floor(t/t_per) + 1. */
+double orc_pulse(int model, double t, double t_per, double t_src, double t_trs, double xi, double zeta)
+{
+    if (model == 0) return 1.0;
+    int nmax = (int)floor(t / t_per) + 1;
+    if (nmax < 0) nmax = 0;
+    double s = 0.0;
+    for (int n = 0; n <= nmax; ++n) {
+        double a = t - n * t_per, b = t - n * t_per - t_src;
+        if (model == 1)
+            s += (a >= 0.0 ? 1.0 : 0.0) - (b >= 0.0 ? 1.0 : 0.0);
+        else
+            s += 0.5 * (erf(xi * (zeta * a / t_trs - 1.0)) - erf(xi * (zeta * b / t_trs - 1.0)));
+    }
+    return s;
+}
+
+/* Attach temperature-dependent materials and the source model to an oracle
+ * built by orc_create (its grid, region map and boundary conditions are
+ * kept; its constant k, C, q are not used by the functions below). */
+void orc_nl_setup(void *p, int n_regions, int K, const double *Tk, const double *lam, const double *cap,
+                  const double *chi, const double *jsq, int model, double t_per, double t_src, double t_trs,
+                  double xi, double zeta, int face_mean)
+{
+    orc_t *o = (orc_t *)p;
+    size_t ncell = (size_t)o->Nr * o->Nz;
+    orc_nl_free(o->nl);
+    orc_nl_t *n = o->nl = (orc_nl_t *)calloc(1, sizeof(orc_nl_t));
+    n->Ts = calloc(ncell, sizeof(double));
+    n->Tn = calloc(ncell, sizeof(double));
+    n->lam_s = calloc(ncell, sizeof(double));
+    n->lam_o = calloc(ncell, sizeof(double));
+    n->cap_x = calloc(ncell, sizeof(double));
+    n->X = calloc(ncell, sizeof(double));
+    n->n_regions = n_regions;
+    n->K = K;
+    n->model = model;
+    n->t_per = t_per, n->t_src = t_src, n->t_trs = t_trs, n->xi = xi, n->zeta = zeta;
+    n->face_mean = face_mean;
+    size_t nt = (size_t)n_regions * K;
+    n->Tk = malloc(nt * sizeof(double));
+    n->lam = malloc(nt * sizeof(double));
+    n->cap = malloc(nt * sizeof(double));
+    n->chi = malloc(nt * sizeof(double));
+    n->jsq = malloc(n_regions * sizeof(double));
+    memcpy(n->Tk, Tk, nt * sizeof(double));
+    memcpy(n->lam, lam, nt * sizeof(double));
+    memcpy(n->cap, cap, nt * sizeof(double));
+    memcpy(n->chi, chi, nt * sizeof(double));
+    memcpy(n->jsq, jsq, n->n_regions * sizeof(double));
+}
+
+/* The per-region laws at one cell. */
+static double lam_at(const orc_t *o, const orc_nl_t *n, size_t c, double T)
+{
+    int m = o->region[c];
+    return table_at(n->Tk + (size_t)m * n->K, n->lam + (size_t)m * n->K, n->K, T);
+}
+static double cap_at(const orc_t *o, const orc_nl_t *n, size_t c, double T)
+{
+    int m = o->region[c];
+    return table_at(n->Tk + (size_t)m * n->K, n->cap + (size_t)m * n->K, n->K, T);
+}
+static double src_at(const orc_t *o, const orc_nl_t *n, size_t c, double T, double pt)
+{
+    int m = o->region[c];
+    return table_at(n->Tk + (size_t)m * n->K, n->chi + (size_t)m * n->K, n->K, T) * n->jsq[m] * pt;
+}
+
+/* Couplings of cell (i,j) (the forms of eqs. "Lambda_r", "Lambda_z", as in
+ * orc_create) from a per-cell conductivity field lam:
+ * out = {Arm, Arp, Azm, Azp, Drl, Drh, Dzl, Dzh}. */
+static void couplings_from(const orc_t *o, const double *lam, int face_mean, int i, int j, double *out)
+{
+    const int Nr = o->Nr, Nz = o->Nz;
+    size_t c = IDX(o, i, j);
+    double l = lam[c], ri = o->rc[i], hb = o->hbar[i], eb = o->etabar[j];
+    for (int a = 0; a < 8; ++a) out[a] = 0.0;
+    if (i > 0 && o->region[IDX(o, i - 1, j)] >= 0)
+        out[0] = o->rf[i] * face_k(lam[IDX(o, i - 1, j)], l, 0.5 * o->dr[i - 1], 0.5 * o->dr[i], face_mean) /
+                 (ri * hb * o->h[i]);
+    if (i < Nr - 1 && o->region[IDX(o, i + 1, j)] >= 0)
+        out[1] = o->rf[i + 1] * face_k(l, lam[IDX(o, i + 1, j)], 0.5 * o->dr[i], 0.5 * o->dr[i + 1], face_mean) /
+                 (ri * hb * o->h[i + 1]);
+    if (j > 0 && o->region[IDX(o, i, j - 1)] >= 0)
+        out[2] = face_k(lam[IDX(o, i, j - 1)], l, 0.5 * o->dz[j - 1], 0.5 * o->dz[j], face_mean) / (eb * o->eta[j]);
+    if (j < Nz - 1 && o->region[IDX(o, i, j + 1)] >= 0)
+        out[3] = face_k(l, lam[IDX(o, i, j + 1)], 0.5 * o->dz[j], 0.5 * o->dz[j + 1], face_mean) / (eb * o->eta[j + 1]);
+    if (i == 0 && o->bc[0] == 1) out[4] = 2.0 * o->rf[0] * l / (ri * hb * o->h[0]);
+    if (i == Nr - 1 && o->bc[1] == 1) out[5] = 2.0 * o->rf[Nr] * l / (ri * hb * o->h[Nr]);
+    if (j == 0 && o->bc[2] == 1) out[6] = 2.0 * l / (eb * o->eta[0]);
+    if (j == Nz - 1 && o->bc[3] == 1) out[7] = 2.0 * l / (eb * o->eta[Nz]);
+}
+
+static void fill_lam(const orc_t *o, const orc_nl_t *n, const double *T, double *lam)
+{
+    for (size_t c = 0; c < (size_t)o->Nr * o->Nz; ++c) lam[c] = o->region[c] >= 0 ? lam_at(o, n, c, T[c]) : 0.0;
+}
+
+/* max |a - b| over the grid (the C-norm of eq. "iter_cond"). */
+static double cnorm_diff(const orc_t *o, const double *a, const double *b)
+{
+    double m = 0.0;
+    for (size_t c = 0; c < (size_t)o->Nr * o->Nz; ++c) {
+        double d = fabs(a[c] - b[c]);
+        if (d > m) m = d;
+    }
+    return m;
+}
+
+/* Half-step 1 by eq. "iter_scheme_eq_1": from the old layer o->T into
+ * o->Tbar.  Xext (optional, per cell) replaces chi(T) j^2 p.  Returns the
+ * number of iterations used, or 0 if s_max were not enough. */
+static int nl_half1(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, int s_max, const double *Xext)
+{
+    const int Nr = o->Nr, Nz = o->Nz;
+    const size_t ncell = (size_t)Nr * Nz;
+    const double half = 0.5 * tau;
+    double *T = o->T, *Ts = n->Ts, *Tn = n->Tn;
+    memcpy(Ts, T, ncell * sizeof(double));  /* T^0 = T */
+    fill_lam(o, n, T, n->lam_o);             /* the explicit z-operator at the old layer */
+    double *a = malloc(sizeof(double) * Nr), *b = malloc(sizeof(double) * Nr);
+    double *cc = malloc(sizeof(double) * Nr), *d = malloc(sizeof(double) * Nr);
+    double *x = malloc(sizeof(double) * Nr), *cw = malloc(sizeof(double) * Nr), *dw = malloc(sizeof(double) * Nr);
+    int used = 0;
+    for (int s = 0; s < s_max; ++s) {
+        fill_lam(o, n, Ts, n->lam_s);
+        for (int j = 0; j < Nz; ++j) {
+            for (int i = 0; i < Nr; ++i) {
+                size_t c = IDX(o, i, j);
+                if (o->region[c] < 0) {
+                    a[i] = 0.0; b[i] = 1.0; cc[i] = 0.0; d[i] = T[c];
+                    continue;
+                }
+                double ks[8], ko[8];
+                couplings_from(o, n->lam_s, n->face_mean, i, j, ks);  /* r-operator at T^s */
+                couplings_from(o, n->lam_o, n->face_mean, i, j, ko);  /* z-operator at T   */
+                double w = cap_at(o, n, c, Ts[c]) / half;
+                double xs = Xext ? Xext[c] : src_at(o, n, c, Ts[c], pt);
+                double t = T[c], lz = 0.0;
+                if (ko[2] != 0.0) lz += ko[2] * (T[IDX(o, i, j - 1)] - t);
+                if (ko[3] != 0.0) lz += ko[3] * (T[IDX(o, i, j + 1)] - t);
+                lz += ko[6] * (o->Tbc[2] - t) + ko[7] * (o->Tbc[3] - t);
+                a[i] = -ks[0];
+                cc[i] = -ks[1];
+                b[i] = w + ks[0] + ks[1] + ks[4] + ks[5];
+                d[i] = w * t + lz + xs + ks[4] * o->Tbc[0] + ks[5] * o->Tbc[1];
+            }
+            orc_thomas(Nr, a, b, cc, d, x, cw, dw);
+            for (int i = 0; i < Nr; ++i) Tn[IDX(o, i, j)] = x[i];
+        }
+        double diff = cnorm_diff(o, Tn, Ts);
+        memcpy(Ts, Tn, ncell * sizeof(double));
+        if (diff < eps) {
+            used = s + 1;
+            break;
+        }
+    }
+    if (used) memcpy(o->Tbar, Ts, ncell * sizeof(double));
+    free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
+    return used;
+}
+
+/* Half-step 2 by eq. "iter_scheme_eq_2": from o->Tbar into n->Tn (left in
+ * n->Ts as well).  Returns the iterations used, or 0. */
+static int nl_half2(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, int s_max, const double *Xext)
+{
+    const int Nr = o->Nr, Nz = o->Nz;
+    const size_t ncell = (size_t)Nr * Nz;
+    const double half = 0.5 * tau;
+    double *Tb = o->Tbar, *Ts = n->Ts, *Tn = n->Tn;
+    memcpy(Ts, Tb, ncell * sizeof(double));  /* T^0 = Tbar */
+    fill_lam(o, n, Tb, n->lam_o);             /* the explicit r-operator at Tbar */
+    for (size_t c = 0; c < ncell; ++c) {      /* rho c_V and X at Tbar */
+        if (o->region[c] < 0) continue;
+        n->cap_x[c] = cap_at(o, n, c, Tb[c]);
+        n->X[c] = Xext ? Xext[c] : src_at(o, n, c, Tb[c], pt);
+    }
+    double *a = malloc(sizeof(double) * Nz), *b = malloc(sizeof(double) * Nz);
+    double *cc = malloc(sizeof(double) * Nz), *d = malloc(sizeof(double) * Nz);
+    double *x = malloc(sizeof(double) * Nz), *cw = malloc(sizeof(double) * Nz), *dw = malloc(sizeof(double) * Nz);
+    int used = 0;
+    for (int s = 0; s < s_max; ++s) {
+        fill_lam(o, n, Ts, n->lam_s);
+        for (int i = 0; i < Nr; ++i) {
+            for (int j = 0; j < Nz; ++j) {
+                size_t c = IDX(o, i, j);
+                if (o->region[c] < 0) {
+                    a[j] = 0.0; b[j] = 1.0; cc[j] = 0.0; d[j] = Tb[c];
+                    continue;
+                }
+                double ks[8], ko[8];
+                couplings_from(o, n->lam_s, n->face_mean, i, j, ks);  /* z-operator at T^s   */
+                couplings_from(o, n->lam_o, n->face_mean, i, j, ko);  /* r-operator at Tbar  */
+                double w = n->cap_x[c] / half;
+                double t = Tb[c], lr = 0.0;
+                if (ko[0] != 0.0) lr += ko[0] * (Tb[IDX(o, i - 1, j)] - t);
+                if (ko[1] != 0.0) lr += ko[1] * (Tb[IDX(o, i + 1, j)] - t);
+                lr += ko[4] * (o->Tbc[0] - t) + ko[5] * (o->Tbc[1] - t);
+                a[j] = -ks[2];
+                cc[j] = -ks[3];
+                b[j] = w + ks[2] + ks[3] + ks[6] + ks[7];
+                d[j] = w * t + lr + n->X[c] + ks[6] * o->Tbc[2] + ks[7] * o->Tbc[3];
+            }
+            orc_thomas(Nz, a, b, cc, d, x, cw, dw);
+            for (int j = 0; j < Nz; ++j) Tn[IDX(o, i, j)] = x[j];
+        }
+        double diff = cnorm_diff(o, Tn, Ts);
+        memcpy(Ts, Tn, ncell * sizeof(double));
+        if (diff < eps) {
+            used = s + 1;
+            break;
+        }
+    }
+    free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
+    return used;
+}
+
+/* One step of length tau from time t (no halving): both iterations; on
+ * success the field advances and it1/it2 hold the iterations used.
+ * Xext: optional per-cell source replacing chi(T) j^2 p (both half-steps).
+ * Returns 1 on success, 0 if either iteration needed more than s_max. */
+int orc_nl_step(void *p, double t, double tau, double eps, int s_max, const double *Xext, int *it1, int *it2)
+{
+    orc_t *o = (orc_t *)p;
+    orc_nl_t *n = o->nl;
+    if (!n) return 0;
+    double pt = orc_pulse(n->model, t + 0.5 * tau, n->t_per, n->t_src, n->t_trs, n->xi, n->zeta);
+    *it1 = nl_half1(o, n, tau, pt, eps, s_max, Xext);
+    *it2 = 0;
+    if (!*it1) return 0;
+    *it2 = nl_half2(o, n, tau, pt, eps, s_max, Xext);
+    if (!*it2) return 0;
+    memcpy(o->T, n->Ts, sizeof(double) * (size_t)o->Nr * o->Nz);
+    return 1;
+}
+
+/* The evolution loop of Sec. 4 from *t to t_end: each step starts from the
+ * estimate (tau_trs inside a transition of the source, tau_base elsewhere),
+ * shortened to land on t_end; a step whose iteration does not converge in
+ * s_max iterations is restarted with tau / 2 (and so on, down to tau_min).
+ * stats (5 doubles): steps, halvings, iterations of half-step 1, of half-step
+ * 2, the smallest tau used.  Returns 0, or -1 when tau fell below tau_min
+ * (the field then holds the last completed step), or -2 after max_steps. */
+int orc_nl_advance(void *p, double *t, double t_end, double tau_base, double tau_trs, double eps, int s_max,
+                   double tau_min, int max_steps, double *stats)
+{
+    orc_nl_t *n = ((orc_t *)p)->nl;
+    if (!n) return -3;
+    for (int a = 0; a < 5; ++a) stats[a] = 0.0;
+    stats[4] = INFINITY;
+    while (*t < t_end) {
+        if (stats[0] >= max_steps) return -2;
+        int trs = 0;
+        if (n->model != 0) {
+            double ph = fmod(*t, n->t_per);
+            trs = ph < n->t_trs || (ph >= n->t_src && ph < n->t_src + n->t_trs);
+        }
+        double tau = trs ? tau_trs : tau_base;
+        int last = tau >= t_end - *t;
+        if (last) tau = t_end - *t;
+        for (;;) {
+            int it1, it2;
+            if (orc_nl_step(p, *t, tau, eps, s_max, NULL, &it1, &it2)) {
+                stats[2] += it1;
+                stats[3] += it2;
+                break;
+            }
+            tau *= 0.5;
+            last = 0;
+            stats[1] += 1.0;
+            if (tau < tau_min) return -1;
+        }
+        *t = last ? t_end : *t + tau;
+        stats[0] += 1.0;
+        if (tau < stats[4]) stats[4] = tau;
+    }
+    return 0;
 }

@@ -58,6 +58,17 @@ def lib():
         L.orc_step_src.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
         L.orc_energy.argtypes = [ctypes.c_void_p, _D, _D, _D]
         L.orc_thomas.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_pulse.restype = ctypes.c_double
+        L.orc_pulse.argtypes = [ctypes.c_int] + [ctypes.c_double] * 6
+        L.orc_nl_setup.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int]
+        L.orc_nl_step.restype = ctypes.c_int
+        L.orc_nl_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  _D, _I, _I]
+        L.orc_nl_advance.restype = ctypes.c_int
+        L.orc_nl_advance.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_max_threads.restype = ctypes.c_int
     return _lib
@@ -80,6 +91,14 @@ def thomas(a, b, c, d):
     dw = np.empty(n)
     lib().orc_thomas(n, _dp(a), _dp(b), _dp(c), _dp(d), _dp(x), _dp(cw), _dp(dw))
     return x
+
+
+def pulse(model: int, t: float, t_per: float, t_src: float, t_trs: float, xi: float = 4.0,
+          zeta: float = 2.0) -> float:
+    """p(t) of the paper's Sec. 2: 0 constant 1, 1 the rectangular pulse
+    train (eq. "unit_model"), 2 its erf-smoothed version (eq. "trans_model")."""
+    return float(lib().orc_pulse(int(model), float(t), float(t_per), float(t_src), float(t_trs), float(xi),
+                                 float(zeta)))
 
 
 def set_threads(n: int) -> None:
@@ -163,3 +182,40 @@ class Oracle:
         e, f, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         lib().orc_energy(self._h, ctypes.byref(e), ctypes.byref(f), ctypes.byref(q))
         return e.value, f.value, q.value
+
+    # ---- temperature-dependent materials, simple iteration, adaptive tau
+    def nl_setup(self, m):
+        """Attach temperature-dependent material tables and the source model
+        (a ``workloads.heat.NlMaterials``); the grid, regions and boundary
+        conditions stay those of the problem."""
+        keep = [np.ascontiguousarray(x, dtype=np.float64) for x in (m.T_knots, m.k, m.C, m.chi, m.j2)]
+        self._keep.extend(keep)
+        Tk, k, C, chi, j2 = keep
+        R, K = Tk.shape
+        lib().orc_nl_setup(self._h, R, K, _dp(Tk), _dp(k), _dp(C), _dp(chi), _dp(j2), int(m.model),
+                           float(m.t_per), float(m.t_src), float(m.t_trs), float(m.xi), float(m.zeta),
+                           int(self.problem.face_mean))
+
+    def nl_step(self, t: float, tau: float, eps: float, s_max: int, X=None):
+        """One step of eqs. "iter_scheme_eq_1/2" from time t (no halving).
+        Returns (ok, iterations of half-step 1, of half-step 2)."""
+        it1, it2 = ctypes.c_int(), ctypes.c_int()
+        xp = None
+        if X is not None:
+            xa = np.ascontiguousarray(X, dtype=np.float64).reshape(self.Nz, self.Nr)
+            self._keep.append(xa)
+            xp = _dp(xa)
+        ok = lib().orc_nl_step(self._h, float(t), float(tau), float(eps), int(s_max), xp, ctypes.byref(it1),
+                               ctypes.byref(it2))
+        return bool(ok), it1.value, it2.value
+
+    def nl_advance(self, t: float, t_end: float, tau_base: float, tau_trs: float, eps: float, s_max: int,
+                   tau_min: float, max_steps: int = 10 ** 9):
+        """The evolution loop of Sec. 4 from t to t_end.  Returns (status, t,
+        stats) with stats = (steps, halvings, iterations 1, iterations 2,
+        smallest tau)."""
+        tt = ctypes.c_double(t)
+        st = np.zeros(5)
+        rc = lib().orc_nl_advance(self._h, ctypes.byref(tt), float(t_end), float(tau_base), float(tau_trs),
+                                  float(eps), int(s_max), float(tau_min), int(max_steps), _dp(st))
+        return int(rc), tt.value, st

@@ -48,6 +48,35 @@ MUTANTS = {
 }
 
 
+# Planted mistakes in the full method (temperature-dependent coefficients,
+# the simple iteration, adaptive tau, the pulsed source); the suite run
+# against them is the nonlinear pins'.
+NL_MUTANTS = {
+    "nl_capacity_at_old_layer_in_half_step_1": ("double w = cap_at(o, n, c, Ts[c]) / half;",
+                                                "double w = cap_at(o, n, c, T[c]) / half;"),
+    "nl_r_operator_at_old_layer_in_half_step_1": (
+        "couplings_from(o, n->lam_s, n->face_mean, i, j, ks);  /* r-operator at T^s */",
+        "couplings_from(o, n->lam_o, n->face_mean, i, j, ks);  /* r-operator at T^s */"),
+    "nl_explicit_z_operator_at_iterate": (
+        "couplings_from(o, n->lam_o, n->face_mean, i, j, ko);  /* z-operator at T   */",
+        "couplings_from(o, n->lam_s, n->face_mean, i, j, ko);  /* z-operator at T   */"),
+    "nl_capacity_iterated_in_half_step_2": ("double w = n->cap_x[c] / half;",
+                                            "double w = cap_at(o, n, c, Ts[c]) / half;"),
+    "nl_z_operator_at_half_layer_in_half_step_2": (
+        "couplings_from(o, n->lam_s, n->face_mean, i, j, ks);  /* z-operator at T^s   */",
+        "couplings_from(o, n->lam_o, n->face_mean, i, j, ks);  /* z-operator at T^s   */"),
+    "nl_source_at_step_start": ("double pt = orc_pulse(n->model, t + 0.5 * tau,", "double pt = orc_pulse(n->model, t,"),
+    "nl_quartered_not_halved": ("tau *= 0.5;", "tau *= 0.25;"),
+    "nl_estimates_swapped": ("double tau = trs ? tau_trs : tau_base;", "double tau = trs ? tau_base : tau_trs;"),
+    "pulse_erf_sign": ("s += 0.5 * (erf(xi * (zeta * a / t_trs - 1.0)) - erf(xi * (zeta * b / t_trs - 1.0)));",
+                       "s += 0.5 * (erf(xi * (zeta * a / t_trs - 1.0)) + erf(xi * (zeta * b / t_trs - 1.0)));"),
+    "pulse_no_half": ("s += 0.5 * (erf(xi * (zeta * a / t_trs - 1.0))", "s += (erf(xi * (zeta * a / t_trs - 1.0))"),
+    "table_wrong_knot": ("return v[k] + (v[k + 1] - v[k]) * (T - Tk[k]) / (Tk[k + 1] - Tk[k]);",
+                         "return v[k] + (v[k + 1] - v[k]) * (T - Tk[k + 1]) / (Tk[k + 1] - Tk[k]);"),
+}
+NL_PINS = os.path.join(ROOT, "tests", "test_oracle_nl_pins.py")
+
+
 def _build(tmp_path, name, src_text):
     c = tmp_path / f"{name}.c"
     so = tmp_path / f"lib_{name}.so"
@@ -56,17 +85,18 @@ def _build(tmp_path, name, src_text):
     return str(so)
 
 
-def _run_pins(so):
+def _run_pins(so, pins=PINS):
     env = dict(os.environ, HEAT_ORACLE_LIB=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider"],
+    r = subprocess.run([sys.executable, "-m", "pytest", pins, "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     return r.returncode, r.stdout[-2000:]
 
 
 def test_unmodified_copy_passes(tmp_path):
     so = _build(tmp_path, "orig", open(SRC).read())
-    rc, out = _run_pins(so)
-    assert rc == 0, out
+    for pins in (PINS, NL_PINS):
+        rc, out = _run_pins(so, pins)
+        assert rc == 0, out
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -77,3 +107,13 @@ def test_planted_mistake_is_caught(tmp_path, name):
     so = _build(tmp_path, name, text.replace(old, new))
     rc, out = _run_pins(so)
     assert rc != 0, f"pins did not catch {name}:\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(NL_MUTANTS))
+def test_planted_mistake_in_the_full_method_is_caught(tmp_path, name):
+    old, new = NL_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    so = _build(tmp_path, name, text.replace(old, new))
+    rc, out = _run_pins(so, NL_PINS)
+    assert rc != 0, f"nonlinear pins did not catch {name}:\n{out}"

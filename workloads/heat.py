@@ -317,3 +317,92 @@ def random_field(p: Problem, seed: int, amp: float = 10.0) -> np.ndarray:
     overwritten by the solvers' own rule, so their value here is irrelevant)."""
     rng = np.random.default_rng(seed)
     return p.T_init + amp * rng.standard_normal((p.Nz, p.Nr))
+
+
+# ------------------------------------------- temperature-dependent materials
+# The paper's k(T), c_V(T) and chi(T) are cited, not printed, so the
+# temperature-dependent runs use synthetic laws with the qualitative shapes of
+# cryogenic materials (conductivity and heat capacity rising with T, the
+# heater's resistivity rising with T), tabulated at knots; the method reads
+# them by linear interpolation (flat beyond the end knots).
+PULSE_CONST, PULSE_RECT, PULSE_ERF = 0, 1, 2
+
+
+@dataclasses.dataclass
+class NlMaterials:
+    """Per-region material tables and the source model of the full method.
+
+    T_knots, k, C, chi: [n_regions, K] -- temperature knots (strictly
+    increasing per region), conductivity W/(m K), volumetric heat capacity
+    rho c_V J/(m^3 K), resistivity Ohm m at the knots.
+    j2: [n_regions] squared current density (I / S_C)^2 in A^2/m^4 (zero
+    outside the heater); the source is X = chi(T) j2 p(t).
+    model, t_per, t_src, t_trs, xi, zeta: the source's time law p(t)
+    (PULSE_CONST: p = 1; PULSE_RECT: the rectangular train; PULSE_ERF: the
+    erf-smoothed train with transition time t_trs).
+    """
+
+    T_knots: np.ndarray
+    k: np.ndarray
+    C: np.ndarray
+    chi: np.ndarray
+    j2: np.ndarray
+    model: int = PULSE_CONST
+    t_per: float = 1.0
+    t_src: float = 1.0
+    t_trs: float = 1.0
+    xi: float = 4.0
+    zeta: float = 2.0
+
+
+def nl_constant(p: Problem) -> NlMaterials:
+    """Temperature-independent tables equal to a problem's constants (one knot;
+    chi = q with j2 = 1), a constant source: the linear method as a special case."""
+    R = len(p.k)
+    return NlMaterials(T_knots=np.zeros((R, 1)), k=np.asarray(p.k, np.float64).reshape(R, 1),
+                       C=np.asarray(p.C, np.float64).reshape(R, 1), chi=np.asarray(p.q, np.float64).reshape(R, 1),
+                       j2=np.ones(R))
+
+
+def nl_power_laws(p: Problem, T_lo: float, T_hi: float, n_knots: int, a_k, a_C, a_chi, T_ref: float,
+                  j2: float, heater: int = 2, **pulse) -> NlMaterials:
+    """Synthetic laws k_m (T/T_ref)^a_k[m], C_m (T/T_ref)^a_C[m], and for the
+    heater chi(T) = chi_0 (T/T_ref)^a_chi with chi_0 j2 = q_heater, sampled at
+    n_knots temperatures spread evenly over [T_lo, T_hi]."""
+    R = len(p.k)
+    Tk = np.linspace(T_lo, T_hi, n_knots)
+    u = Tk / T_ref
+    k = np.array([p.k[m] * u ** a_k[m] for m in range(R)])
+    C = np.array([p.C[m] * u ** a_C[m] for m in range(R)])
+    chi = np.zeros((R, n_knots))
+    jj = np.zeros(R)
+    chi[heater] = p.q[heater] / j2 * u ** a_chi
+    jj[heater] = j2
+    return NlMaterials(T_knots=np.tile(Tk, (R, 1)), k=k, C=C, chi=chi, j2=jj, **pulse)
+
+
+def nl_linear_laws(p: Problem, beta_k: float, beta_C: float, T_lo: float, T_hi: float) -> NlMaterials:
+    """k_m (1 + beta_k T), C_m (1 + beta_C T) as two-knot tables over [T_lo, T_hi]
+    (linear interpolation reproduces a linear law exactly inside the range);
+    the source is the problem's q, constant."""
+    R = len(p.k)
+    Tk = np.array([T_lo, T_hi])
+    k = np.array([[p.k[m] * (1.0 + beta_k * T) for T in Tk] for m in range(R)])
+    C = np.array([[p.C[m] * (1.0 + beta_C * T) for T in Tk] for m in range(R)])
+    chi = np.array([[p.q[m], p.q[m]] for m in range(R)])
+    return NlMaterials(T_knots=np.tile(Tk, (R, 1)), k=k, C=C, chi=chi, j2=np.ones(R))
+
+
+def paper_example_nl(Nr_cells=(800, 200, 200, 10), Nz_cells=(80, 20)) -> tuple:
+    """The paper's own example (Sec. 5) as far as it is given: the graded
+    1210 x 100 grid without terminal cap, T0 = 4.2 K, the pulsed source with
+    t_per = 0.1 s, t_src = 0.01 s, t_trs = 1e-4 s, xi = 4, zeta = 2.  The
+    material laws are synthetic (see nl_power_laws): k and C rising with T
+    (exponents 1 and 3, the low-temperature shapes of metals' conductivity and
+    Debye heat capacity) around seeded magnitudes, the heater's resistivity
+    rising linearly.  Returns (problem, materials)."""
+    p = config_paper_grid()
+    p = p.copy(r_cells=np.array(Nr_cells, np.int32), z_cells=np.array(Nz_cells, np.int32))
+    m = nl_power_laws(p, 4.2, 60.0, 9, a_k=[1.0] * N_REGIONS, a_C=[3.0] * N_REGIONS, a_chi=1.0, T_ref=4.2,
+                      j2=1.0, model=PULSE_ERF, t_per=0.1, t_src=0.01, t_trs=1e-4, xi=4.0, zeta=2.0)
+    return p, m
