@@ -275,6 +275,45 @@ def time_config1(steps=200, warmup=10):
             "note": "64 KB field, resident in L2: the HBM roofline does not apply"}
 
 
+def time_full_method(window_steps=None):
+    """The paper's full method (temperature-dependent laws, simple iteration,
+    adaptive tau, erf-smoothed pulsed source) on its example shape: the graded
+    1210 x 100 grid without terminal cap, t_per 0.1 s, t_src 0.01 s, t_trs
+    1e-4 s, the per-step estimates t_src/100 and t_trs/1000, synthetic laws.
+    Timed: the window from 3 base steps before the first switch-off through
+    its transition (1000 steps of t_trs/1000) and 5 base steps after it, the
+    stretch where the method takes most of its steps per period; wall time
+    of heat_nl_advance (it synchronizes once per batch of iterations)."""
+    import torch
+    from paper_1912_03744_gb300 import HeatNl
+    p, m = H.paper_example_nl()
+    m.j2 = m.j2 * 4e3
+    kw = dict(eps=1e-9, s_max=20, tau_base=m.t_src / 100, tau_trs=m.t_trs / 1000, tau_min=1e-12)
+    s = HeatNl(p, m, **kw)
+    s.set_time(0.0)
+    s.advance(2e-5)  # warm-up: 200 transition steps
+    t0 = m.t_src - 3 * kw["tau_base"]
+    t_end = m.t_src + m.t_trs + 5 * kw["tau_base"]
+    s.set_time(t0)
+    torch.cuda.synchronize()
+    l0 = s.launches()
+    w0 = time.perf_counter()
+    st = s.advance(t_end)
+    w = time.perf_counter() - w0
+    launches = s.launches() - l0
+    T = s.field()
+    s.close()
+    cells = p.Nr * p.Nz
+    its = st["iters1"] + st["iters2"]
+    return {"workload": "paper example shape: graded 1210x100, no cap, erf pulse t_per 0.1 s, t_src 0.01 s, "
+                        "t_trs 1e-4 s, synthetic T-dependent laws, FP64",
+            "window_s": [t0, t_end], "steps": st["steps"], "halvings": st["halvings"],
+            "iterations_per_half_step": its / (2 * st["steps"]), "wall_s": w, "steps_per_s": st["steps"] / w,
+            "cell_steps_per_s": cells * st["steps"] / w, "cell_iterations_per_s": cells * its / w,
+            "launches": launches, "finite": bool(np.isfinite(T).all()),
+            "bound": "latency: one thread per line (100 r-lines of 1210 cells), a host read per iteration batch"}
+
+
 def step_roofline(cells_active, word, ms_per_step):
     """Whole-step algorithmic bandwidth (read + write of every active cell in
     each of the two sweeps) against the measured copy bandwidth."""
@@ -560,6 +599,7 @@ def main():
     side_t = time_gpu(p, other, side_steps, args.warmup, flush)
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
     c1 = time_config1()
+    full = time_full_method()
     ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning)
     c4 = None if args.no_config4 else time_config4(args.config4_steps, args.warmup)
     surr = None if args.no_surrogate else time_surrogate(args.surrogate_train, args.surrogate_epochs)
@@ -629,6 +669,7 @@ def main():
         "gpu_launches": main_t["launches"],
         "clocks": clk.summary(),
         "config1": c1,
+        "full_method": full,
         "ensemble": ens,
         "config4": c4,
         "surrogate": surr,

@@ -55,6 +55,7 @@ extern "C" {
 #define HEAT_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up               */
 #define HEAT_ERR_OOM (-5)       /* device allocation failed                         */
 #define HEAT_ERR_TOO_LARGE (-6) /* size beyond a fixed capacity (heat_energy_noalloc) */
+#define HEAT_ERR_NOCONV (-7)    /* the simple iteration did not converge (heat_nl_*) */
 
 /* ---- precision of the stored field and the line solves ---- */
 #define HEAT_FP64 0             /* FP64 field, FP64 line solves                     */
@@ -251,6 +252,100 @@ int heat_batch_get_tuning(heat_batch *b, int *rK, int *band, int *zwpb);
 int heat_batch_launches_per_step(heat_batch *b);
 
 void heat_batch_destroy(heat_batch *b);
+
+/* ---- the full method: temperature-dependent materials, the simple
+ * iteration, adaptive tau and the pulsed source (FP64) ----
+ *   Sec. 2, eq. "main_eq":   k, C = rho c_V and the source depend on T.
+ *   Sec. 2, eq. "source":    X = chi(T) j^2 p(t): chi the region's resistivity,
+ *                            j its current density (the printed I^2/S_C read as
+ *                            (I/S_C)^2, a power per volume).
+ *   Sec. 2, eqs. "unit_model", "trans_model": p(t), the rectangular pulse
+ *                            train or its erf-smoothed version.
+ *   Sec. 3, eqs. "iter_scheme_eq_1", "iter_scheme_eq_2", "iter_cond": each
+ *                            half-step iterates T^s -> T^{s+1} until
+ *                            max |T^{s+1} - T^s| < eps.  Half-step 1: C, X and
+ *                            the r-couplings at T^s, the explicit z-operator at
+ *                            the old layer.  Half-step 2: the z-couplings at
+ *                            T^s, C, X and the explicit r-operator at Tbar.
+ *   Sec. 3 (last paragraph) and Sec. 4: s_max iterations without convergence
+ *                            halve tau and restart the step; every step starts
+ *                            from the estimate t_trs/1000 inside a transition
+ *                            of the source, t_src/100 elsewhere.
+ * Readings: material laws are per-region tables at temperature knots, linear
+ * between knots and flat beyond the ends (the paper's laws are cited, not
+ * printed); face conductivities are the harmonic (or arithmetic) means of the
+ * two cells' own conductivities; the source is taken at t + tau/2; theta(0) = 1
+ * in u(t); a transition is t mod t_per in [0, t_trs) or [t_src, t_src + t_trs);
+ * heat_nl_advance shortens a step outside a transition to end at the next
+ * switch (n t_per or n t_per + t_src; a phase within 1e-9 t_per of a switch
+ * counts as at it), and its last step to end at t_end.
+ * Geometry, boundary conditions, layout ([Nz][Nr] doubles), ownership and
+ * stream rules are those of heat_create; the field is FP64 and holds T. */
+typedef struct heat_nl heat_nl; /* opaque, library-owned */
+
+typedef struct {
+    int n_regions, n_knots;  /* 1 <= n_knots <= 1024                         */
+    const double *T_knots;   /* [n_regions][n_knots], increasing per region  */
+    const double *k;         /* conductivity at the knots, > 0               */
+    const double *C;         /* volumetric heat capacity at the knots, > 0   */
+    const double *chi;       /* resistivity at the knots                     */
+    const double *j2;        /* [n_regions] squared current density          */
+    double T_init;           /* uniform initial temperature                  */
+} heat_nl_materials;
+
+#define HEAT_PULSE_CONST 0 /* p = 1                                       */
+#define HEAT_PULSE_RECT 1  /* rectangular train u(t), eq. "unit_model"    */
+#define HEAT_PULSE_ERF 2   /* smoothed train v(t), eq. "trans_model"      */
+typedef struct {
+    int model;
+    double t_per, t_src, t_trs; /* period, heating time <= t_per, transition time (> 0 unless CONST) */
+    double xi, zeta;            /* the smoothing constants of v(t) (the paper: 4 and 2) */
+} heat_pulse;
+
+typedef struct {
+    double eps;       /* stop of the iteration: max |T^{s+1} - T^s| < eps (K), > 0     */
+    int s_max;        /* iterations before tau is halved, 1..4096                      */
+    double tau_base;  /* step estimate outside transitions (the paper: t_src/100)     */
+    double tau_trs;   /* step estimate inside transitions (the paper: t_trs/1000)     */
+    double tau_min;   /* heat_nl_advance gives up below this step                     */
+    int face_mean;    /* HEAT_HARMONIC | HEAT_ARITH                                    */
+} heat_nl_options;
+
+typedef struct {
+    long long steps, halvings, iters1, iters2; /* iterations summed over the steps */
+    double tau_smallest;                       /* the shortest step taken          */
+} heat_nl_stats;
+
+/* Grid, regions and tables; T = T_init, time 0.  Errors: HEAT_ERR_ARG (bad
+ * geometry as heat_create, Nr > HEAT_NL_MAX_NR, non-increasing knots, k or
+ * C <= 0, bad options), HEAT_ERR_OOM, HEAT_ERR_CUDA.  On error *out is NULL.
+ * Limit: an r-line is assembled and solved in one warp's shared memory (five
+ * rows of Nr doubles), so Nr <= HEAT_NL_MAX_NR. */
+#define HEAT_NL_MAX_NR 5632
+int heat_nl_create(const heat_geometry *geom, const heat_nl_materials *mat, const heat_pulse *pulse,
+                   const heat_nl_options *opt, void *stream, heat_nl **out);
+
+/* One step of length tau from the current time, without halving.  it1, it2
+ * (may be NULL): iterations of the two half-steps.  HEAT_ERR_NOCONV if either
+ * needed more than s_max (field and time unchanged).  Synchronizes. */
+int heat_nl_step(heat_nl *s, double tau, int *it1, int *it2);
+
+/* The evolution loop of Sec. 4 from the current time to t_end (at most
+ * max_steps steps; check heat_nl_time for where it stopped).  stats may be
+ * NULL.  HEAT_ERR_NOCONV when a step needed tau < tau_min (the field holds the
+ * last completed step).  Synchronizes. */
+int heat_nl_advance(heat_nl *s, double t_end, long long max_steps, heat_nl_stats *stats);
+
+int heat_nl_time(heat_nl *s, double *t);
+int heat_nl_set_time(heat_nl *s, double t);
+/* Field I/O as heat_field / heat_set_field; heat_nl_half_field returns the
+ * half layer Tbar of the last completed step. */
+int heat_nl_field(heat_nl *s, double *out, size_t n, int on_device);
+int heat_nl_half_field(heat_nl *s, double *out, size_t n, int on_device);
+int heat_nl_set_field(heat_nl *s, const double *in, size_t n, int on_device);
+/* Grid size and the number of kernel launches so far. */
+int heat_nl_info(heat_nl *s, int *Nr, int *Nz, long long *launches);
+void heat_nl_destroy(heat_nl *s);
 
 const char *heat_strerror(int status);
 

@@ -486,7 +486,11 @@ void orc_energy(void *p, double *E, double *Phi, double *Q)
  * or arithmetic: the same two readings as the constant case); the source is
  * evaluated at t_k + tau/2 in both half-steps; the last step is shortened to
  * land on t_end; theta(0) = 1 in u(t); a transition is the first t_trs after
- * a switch-on (t mod t_per in [0, t_trs)) or switch-off ([t_src, t_src + t_trs)).
+ * a switch-on (t mod t_per in [0, t_trs)) or switch-off ([t_src, t_src + t_trs));
+ * a step outside a transition is shortened to end at the next switch, so that
+ * no step passes over a transition (a phase within 1e-9 t_per of a switch
+ * counts as at it, so that rounding of the landing time cannot leave a
+ * vanishing step).
  * ==================================================================== */
 
 typedef struct orc_nl {
@@ -640,12 +644,15 @@ static int nl_half1(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
     double *T = o->T, *Ts = n->Ts, *Tn = n->Tn;
     memcpy(Ts, T, ncell * sizeof(double));  /* T^0 = T */
     fill_lam(o, n, T, n->lam_o);             /* the explicit z-operator at the old layer */
-    double *a = malloc(sizeof(double) * Nr), *b = malloc(sizeof(double) * Nr);
-    double *cc = malloc(sizeof(double) * Nr), *d = malloc(sizeof(double) * Nr);
-    double *x = malloc(sizeof(double) * Nr), *cw = malloc(sizeof(double) * Nr), *dw = malloc(sizeof(double) * Nr);
     int used = 0;
     for (int s = 0; s < s_max; ++s) {
         fill_lam(o, n, Ts, n->lam_s);
+#pragma omp parallel
+        {
+        double *a = malloc(sizeof(double) * Nr), *b = malloc(sizeof(double) * Nr);
+        double *cc = malloc(sizeof(double) * Nr), *d = malloc(sizeof(double) * Nr);
+        double *x = malloc(sizeof(double) * Nr), *cw = malloc(sizeof(double) * Nr), *dw = malloc(sizeof(double) * Nr);
+#pragma omp for schedule(static)
         for (int j = 0; j < Nz; ++j) {
             for (int i = 0; i < Nr; ++i) {
                 size_t c = IDX(o, i, j);
@@ -670,6 +677,8 @@ static int nl_half1(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
             orc_thomas(Nr, a, b, cc, d, x, cw, dw);
             for (int i = 0; i < Nr; ++i) Tn[IDX(o, i, j)] = x[i];
         }
+        free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
+        }
         double diff = cnorm_diff(o, Tn, Ts);
         memcpy(Ts, Tn, ncell * sizeof(double));
         if (diff < eps) {
@@ -678,7 +687,6 @@ static int nl_half1(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
         }
     }
     if (used) memcpy(o->Tbar, Ts, ncell * sizeof(double));
-    free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
     return used;
 }
 
@@ -697,12 +705,15 @@ static int nl_half2(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
         n->cap_x[c] = cap_at(o, n, c, Tb[c]);
         n->X[c] = Xext ? Xext[c] : src_at(o, n, c, Tb[c], pt);
     }
-    double *a = malloc(sizeof(double) * Nz), *b = malloc(sizeof(double) * Nz);
-    double *cc = malloc(sizeof(double) * Nz), *d = malloc(sizeof(double) * Nz);
-    double *x = malloc(sizeof(double) * Nz), *cw = malloc(sizeof(double) * Nz), *dw = malloc(sizeof(double) * Nz);
     int used = 0;
     for (int s = 0; s < s_max; ++s) {
         fill_lam(o, n, Ts, n->lam_s);
+#pragma omp parallel
+        {
+        double *a = malloc(sizeof(double) * Nz), *b = malloc(sizeof(double) * Nz);
+        double *cc = malloc(sizeof(double) * Nz), *d = malloc(sizeof(double) * Nz);
+        double *x = malloc(sizeof(double) * Nz), *cw = malloc(sizeof(double) * Nz), *dw = malloc(sizeof(double) * Nz);
+#pragma omp for schedule(static)
         for (int i = 0; i < Nr; ++i) {
             for (int j = 0; j < Nz; ++j) {
                 size_t c = IDX(o, i, j);
@@ -726,6 +737,8 @@ static int nl_half2(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
             orc_thomas(Nz, a, b, cc, d, x, cw, dw);
             for (int j = 0; j < Nz; ++j) Tn[IDX(o, i, j)] = x[j];
         }
+        free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
+        }
         double diff = cnorm_diff(o, Tn, Ts);
         memcpy(Ts, Tn, ncell * sizeof(double));
         if (diff < eps) {
@@ -733,7 +746,6 @@ static int nl_half2(orc_t *o, orc_nl_t *n, double tau, double pt, double eps, in
             break;
         }
     }
-    free(a); free(b); free(cc); free(d); free(x); free(cw); free(dw);
     return used;
 }
 
@@ -773,11 +785,16 @@ int orc_nl_advance(void *p, double *t, double t_end, double tau_base, double tau
     while (*t < t_end) {
         if (stats[0] >= max_steps) return -2;
         int trs = 0;
+        double to_switch = INFINITY;
         if (n->model != 0) {
-            double ph = fmod(*t, n->t_per);
-            trs = ph < n->t_trs || (ph >= n->t_src && ph < n->t_src + n->t_trs);
+            /* phase in the period; within tol of a switch counts as at it */
+            double tol = 1e-9 * n->t_per, ph = fmod(*t, n->t_per);
+            if (n->t_per - ph < tol) ph = 0.0;
+            trs = ph < n->t_trs || (ph >= n->t_src - tol && ph < n->t_src + n->t_trs);
+            if (!trs) to_switch = (ph < n->t_src ? n->t_src : n->t_per) - ph;
         }
         double tau = trs ? tau_trs : tau_base;
+        if (tau > to_switch) tau = to_switch; /* do not step over a transition */
         int last = tau >= t_end - *t;
         if (last) tau = t_end - *t;
         for (;;) {

@@ -3,5 +3,5 @@
 The compute path is libheat.so (CUDA kernels behind the C ABI in
 include/heat.h); this package is its thin Python binding.
 """
-from .heat import HeatBatch, HeatSolver, HeatError, load, LIB_PATH, SYMBOLS  # noqa: F401
+from .heat import HeatBatch, HeatError, HeatNl, HeatSolver, load, LIB_PATH, SYMBOLS  # noqa: F401
 from .surrogate import Surrogate, SURR_SYMBOLS  # noqa: F401

@@ -247,6 +247,7 @@ const char *heat_strerror(int status)
     case HEAT_ERR_TIMEOUT: return "device wait timed out";
     case HEAT_ERR_OOM: return "device out of memory";
     case HEAT_ERR_TOO_LARGE: return "size beyond a fixed capacity";
+    case HEAT_ERR_NOCONV: return "iteration did not converge";
     default: return "unknown status";
     }
 }

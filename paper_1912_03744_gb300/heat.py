@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libheat.so")
 
 HEAT_OK = 0
 STATUS = {0: "ok", -1: "HEAT_ERR_ARG", -2: "HEAT_ERR_CUDA", -3: "HEAT_ERR_NONFINITE",
-          -4: "HEAT_ERR_TIMEOUT", -5: "HEAT_ERR_OOM", -6: "HEAT_ERR_TOO_LARGE"}
+          -4: "HEAT_ERR_TIMEOUT", -5: "HEAT_ERR_OOM", -6: "HEAT_ERR_TOO_LARGE", -7: "HEAT_ERR_NOCONV"}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 NUMPY_DTYPE = {"fp64": np.float64, "fp32": np.float32, "fp32_refined": np.float32}
 
@@ -25,7 +25,9 @@ SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field"
            "heat_info", "heat_launches_per_step", "heat_sync", "heat_destroy", "heat_strerror",
            "heat_energy_noalloc", "heat_batch_create", "heat_batch_member", "heat_batch_step", "heat_batch_sync",
            "heat_batch_tune", "heat_batch_set_tuning", "heat_batch_get_tuning", "heat_batch_launches_per_step",
-           "heat_batch_destroy", "heat_batch_set_dt"]
+           "heat_batch_destroy", "heat_batch_set_dt",
+           "heat_nl_create", "heat_nl_step", "heat_nl_advance", "heat_nl_time", "heat_nl_set_time", "heat_nl_field",
+           "heat_nl_half_field", "heat_nl_set_field", "heat_nl_info", "heat_nl_destroy"]
 
 
 class HeatError(RuntimeError):
@@ -56,6 +58,26 @@ class _Materials(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("face_mean", ctypes.c_int)]
+
+
+class _NlMaterials(ctypes.Structure):
+    _fields_ = [("n_regions", ctypes.c_int), ("n_knots", ctypes.c_int)] + \
+        [(n, ctypes.POINTER(ctypes.c_double)) for n in ("T_knots", "k", "C", "chi", "j2")] + \
+        [("T_init", ctypes.c_double)]
+
+
+class _Pulse(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int)] + [(n, ctypes.c_double) for n in ("t_per", "t_src", "t_trs", "xi", "zeta")]
+
+
+class _NlOptions(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("s_max", ctypes.c_int), ("tau_base", ctypes.c_double),
+                ("tau_trs", ctypes.c_double), ("tau_min", ctypes.c_double), ("face_mean", ctypes.c_int)]
+
+
+class _NlStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("halvings", ctypes.c_longlong), ("iters1", ctypes.c_longlong),
+                ("iters2", ctypes.c_longlong), ("tau_smallest", ctypes.c_double)]
 
 
 _lib = None
@@ -97,6 +119,18 @@ def load():
         L.heat_batch_launches_per_step.argtypes = [vp]
         L.heat_batch_destroy.argtypes = [vp]
         L.heat_batch_destroy.restype = None
+        L.heat_nl_create.argtypes = [ctypes.POINTER(_Geometry), ctypes.POINTER(_NlMaterials), ctypes.POINTER(_Pulse),
+                                     ctypes.POINTER(_NlOptions), vp, ctypes.POINTER(vp)]
+        L.heat_nl_step.argtypes = [vp, ctypes.c_double, ip, ip]
+        L.heat_nl_advance.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(_NlStats)]
+        L.heat_nl_time.argtypes = [vp, dp]
+        L.heat_nl_set_time.argtypes = [vp, ctypes.c_double]
+        L.heat_nl_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.heat_nl_half_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.heat_nl_set_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.heat_nl_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_nl_destroy.argtypes = [vp]
+        L.heat_nl_destroy.restype = None
         _lib = L
     return _lib
 
@@ -334,3 +368,98 @@ class HeatBatch:
 
     def launches_per_step(self) -> int:
         return int(load().heat_batch_launches_per_step(self._h))
+
+
+def _marshal_nl(p, m, eps, s_max, tau_base, tau_trs, tau_min, keep):
+    """heat_geometry, heat_nl_materials, heat_pulse and heat_nl_options of a
+    problem and its ``workloads.heat.NlMaterials``."""
+    geo, _ = _marshal(p, keep)
+    Tk, k, C, chi = (np.ascontiguousarray(x, dtype=np.float64) for x in (m.T_knots, m.k, m.C, m.chi))
+    j2 = np.ascontiguousarray(m.j2, dtype=np.float64)
+    keep.extend([Tk, k, C, chi, j2])
+    R, K = Tk.shape
+    dp = ctypes.POINTER(ctypes.c_double)
+    mat = _NlMaterials(R, K, Tk.ctypes.data_as(dp), k.ctypes.data_as(dp), C.ctypes.data_as(dp),
+                       chi.ctypes.data_as(dp), j2.ctypes.data_as(dp), float(p.T_init))
+    pulse = _Pulse(int(m.model), float(m.t_per), float(m.t_src), float(m.t_trs), float(m.xi), float(m.zeta))
+    opt = _NlOptions(float(eps), int(s_max), float(tau_base), float(tau_trs), float(tau_min),
+                     int(getattr(p, "face_mean", 0)))
+    return geo, mat, pulse, opt
+
+
+class HeatNl:
+    """The paper's full method on the GPU (wraps heat_nl_*): temperature-
+    dependent materials, the simple iteration, adaptive tau, the pulsed
+    source; FP64.  ``materials``: a ``workloads.heat.NlMaterials``."""
+
+    def __init__(self, problem, materials, eps=1e-9, s_max=20, tau_base=1.0, tau_trs=1.0, tau_min=1e-12,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("HeatNl needs a CUDA GPU; there is no CPU path")
+        L = load()
+        self._keep = []
+        geo, mat, pulse, opt = _marshal_nl(problem, materials, eps, s_max, tau_base, tau_trs, tau_min, self._keep)
+        sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _current_stream_handle()
+        h = ctypes.c_void_p()
+        _check("heat_nl_create", L.heat_nl_create(ctypes.byref(geo), ctypes.byref(mat), ctypes.byref(pulse),
+                                                  ctypes.byref(opt), sh, ctypes.byref(h)))
+        self._h = h
+        nr, nz = ctypes.c_int(), ctypes.c_int()
+        _check("heat_nl_info", L.heat_nl_info(h, ctypes.byref(nr), ctypes.byref(nz), None))
+        self.Nr, self.Nz = nr.value, nz.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().heat_nl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, tau: float):
+        """One step of length tau (no halving); returns the iterations of the
+        two half-steps.  Raises HeatError (HEAT_ERR_NOCONV) if s_max is not enough."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check("heat_nl_step", load().heat_nl_step(self._h, float(tau), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def advance(self, t_end: float, max_steps: int = 2 ** 62):
+        """The evolution loop of Sec. 4 up to t_end; returns its statistics."""
+        st = _NlStats()
+        _check("heat_nl_advance", load().heat_nl_advance(self._h, float(t_end), int(max_steps), ctypes.byref(st)))
+        return {"steps": st.steps, "halvings": st.halvings, "iters1": st.iters1, "iters2": st.iters2,
+                "tau_smallest": st.tau_smallest}
+
+    @property
+    def time(self) -> float:
+        t = ctypes.c_double()
+        _check("heat_nl_time", load().heat_nl_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    def set_time(self, t: float):
+        _check("heat_nl_set_time", load().heat_nl_set_time(self._h, float(t)))
+
+    def _get(self, fn):
+        out = np.empty((self.Nz, self.Nr))
+        _check(fn, getattr(load(), fn)(self._h, out.ctypes.data_as(ctypes.c_void_p), self.Nr * self.Nz, 0))
+        return out
+
+    def field(self):
+        return self._get("heat_nl_field")
+
+    def half_field(self):
+        return self._get("heat_nl_half_field")
+
+    def set_field(self, T):
+        a = np.ascontiguousarray(T, dtype=np.float64).reshape(self.Nz, self.Nr)
+        _check("heat_nl_set_field", load().heat_nl_set_field(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                             self.Nr * self.Nz, 0))
+
+    def launches(self) -> int:
+        n = ctypes.c_longlong()
+        _check("heat_nl_info", load().heat_nl_info(self._h, None, None, ctypes.byref(n)))
+        return n.value

@@ -318,3 +318,22 @@ def test_one_column_half_step_is_explicit_in_z_at_the_old_layer():
     flux[1:-1] = kf * (T[1:] - T[:-1]) / dz
     Tbar = T + 0.5 * tau * (flux[1:] - flux[:-1]) / dz / C
     np.testing.assert_allclose(o.half_field()[:, 0], Tbar, rtol=1e-13)
+
+
+def test_no_step_passes_over_a_transition():
+    """A base step that would cross the switch-off ends at it, and the
+    transition then runs at t_trs/1000: from 2.5 base steps before the switch,
+    two full steps and a half one reach it, 1000 transition steps follow, then
+    base steps to t_end."""
+    p = H.config1()
+    m = H.nl_constant(p)
+    m.model, m.t_per, m.t_src, m.t_trs = H.PULSE_ERF, T_PER, T_SRC, T_TRS
+    o = Oracle(p)
+    o.nl_setup(m)
+    base = T_SRC / 100
+    t0 = T_SRC - 2.5 * base
+    t_end = T_SRC + T_TRS + 3 * base
+    rc, t, st = o.nl_advance(t0, t_end, base, T_TRS / 1000, 1e-9, 10, 1e-12)
+    assert rc == 0 and t == t_end
+    assert abs(st[0] - (3 + 1000 + 3)) <= 1, st
+    assert st[4] < 0.6 * base and st[4] >= T_TRS / 1000 * (1 - 1e-9)
