@@ -79,6 +79,24 @@ int upload_tab(heat_ctx *ctx, const HostTab &T, DevTab &D)
         auto G = [&](int a) { return (const float *)(q + a * n); };
         D.t32 = LineTab<float>{G(0), G(1), G(2), G(3), G(4), G(5), G(6), G(7), G(8), G(9), G(10), G(11), G(12), G(13)};
     }
+    std::vector<float2> h2;
+    if (ctx->precision == HEAT_FP32_REFINED) {
+        // the residual's coefficients as FP32 pairs (hi, lo): am, ap, dl, dh, q, b, m, p
+        const std::vector<double> *src2[8] = {&T.am, &T.ap, &T.dl, &T.dh, &T.q, &T.b, &T.m, &T.p};
+        if (!D.buf2) HEAT_CHECK(cudaMalloc(&D.buf2, 8 * n * sizeof(float2)));
+        h2.resize(8 * n);
+        for (int a = 0; a < 8; ++a)
+            for (size_t x = 0; x < n; ++x) {
+                const double v = (*src2[a])[x];
+                const float hi = (float)v;
+                h2[a * n + x] = make_float2(hi, (float)(v - (double)hi));
+            }
+        HEAT_CHECK(cudaMemcpyAsync(D.buf2, h2.data(), h2.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+        const float2 *q2 = D.buf2;
+        auto P = [&](int a) { return q2 + a * n; };
+        D.t2 = LineTab2{P(0), P(1), P(2), P(3), P(4), P(5), P(6), P(7)};
+    }
     // host vectors are freed on return: the copies must complete first
     HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
     return HEAT_OK;
@@ -203,7 +221,7 @@ int upload_rline(heat_ctx *ctx)
 void free_ctx(heat_ctx *ctx)
 {
     if (!ctx) return;
-    void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32,   ctx->dZ.buf64,   ctx->dZ.buf32, ctx->d_rowcls,
+    void *bufs[] = {ctx->dR.buf64, ctx->dR.buf32,   ctx->dZ.buf64,   ctx->dZ.buf32, ctx->dR.buf2, ctx->dZ.buf2, ctx->d_rowcls,
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
                     ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,

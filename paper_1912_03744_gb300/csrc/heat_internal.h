@@ -67,6 +67,13 @@ struct LineTab64 {
     const double *cap, *dsum, *dbc;
 };
 
+// The FP64 tables the refined path's residual reads, each value v as the
+// pair (hi, lo) of FP32 numbers with hi = fl32(v), lo = fl32(v - hi): v to
+// about 2^-48 relative (see Pair in heat_kernels.cuh).
+struct LineTab2 {
+    const float2 *am, *ap, *dl, *dh, *q, *b, *m, *p;
+};
+
 // Tables of the line-team r-sweep (heat_rline.cuh) for chunks of K cells,
 // teams of LW lanes and nseg segments of LW*K cells per line (Npad = nseg LW K
 // cells, the padding cells having all-zero entries).  Per row class:
@@ -114,6 +121,7 @@ struct SweepArgs {
     const int *rowcls, *colcls;
     LineTab<real> R, Z;
     LineTab64 R64, Z64;
+    LineTab2 R2, Z2;          // refined path: the residual's coefficients as FP32 pairs
     RLine<real> rl;           // line-team r-sweep tables (tA == nullptr: not built)
     BcVals bc;
     const real *pkA, *pkB, *chk;
@@ -165,9 +173,11 @@ struct HostTab {
 struct DevTab {
     double *buf64 = nullptr;  // 20 fields x n_class x N doubles
     float *buf32 = nullptr;   // 14 fields x n_class x N floats
+    float2 *buf2 = nullptr;   // refined path: 8 fields x n_class x N FP32 pairs
     LineTab<double> t64{};
     LineTab<float> t32{};
     LineTab64 full{};
+    LineTab2 t2{};
 };
 
 // Column partition of the z-sweep.  Every column is cut into chunks of Rc

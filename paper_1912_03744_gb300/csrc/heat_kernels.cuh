@@ -18,8 +18,9 @@
 //       (th_nb - th).  In FP32 the factorization error then scales with
 //       |delta| instead of |th|, and a steady state is reproduced exactly.
 // Refined FP32 path: after the FP32 solve, the residual of the increment
-// system is formed in FP64 from FP64 coefficients and one more FP32 solve
-// corrects delta (one step of mixed-precision iterative refinement).
+// system is formed in extended precision (FP32 pairs, about 44 bits) from the
+// FP64 coefficients and one more FP32 solve corrects delta (one step of
+// mixed-precision iterative refinement).
 //
 // r-sweep (rows are contiguous).  One line per block (or per warp segment
 // for short rows); thread g owns the K consecutive cells [gK, gK+K).  Each
@@ -54,6 +55,44 @@ enum { MODE_LIT = 0, MODE_DELTA = 1, MODE_REFINE = 2, MODE_CORR = 3 };
 
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---- extended precision from FP32 pairs (the refined path's residual).
+// A value is carried as hi + lo, two FP32 numbers.  Sums and products use the
+// error-free transformations TwoSum (Knuth: s + e = a + b exactly) and
+// TwoProduct (one FMA: p + e = a b exactly), so the residual of a line
+// system -- a sum of about ten terms that cancel to a small remainder -- keeps
+// about 44 significant bits, far more than the one FP32 correction needs.
+// GB300's FP64 units retire two FMAs per clock per SM against 128 FP32 ones;
+// the ~17 FP32 operations a term costs here are a tenth of the FP64 time.
+// The _rn intrinsics keep the compiler from fusing or reordering them.
+struct Pair {
+    float hi, lo;
+};
+__device__ __forceinline__ Pair two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// acc += c x, c = (c.x, c.y) a pair, x an FP32 value
+__device__ __forceinline__ void pair_add_cx(Pair &acc, float2 c, float x)
+{
+    const float p = __fmul_rn(c.x, x);
+    const float small = __fmaf_rn(c.y, x, __fmaf_rn(c.x, x, -p));
+    const Pair t = two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, small));
+}
+// acc += c (u - v), the difference of two FP32 values taken exactly
+__device__ __forceinline__ void pair_add_cdiff(Pair &acc, float2 c, float u, float v)
+{
+    const Pair d = two_sum(u, -v);
+    const float p = __fmul_rn(c.x, d.hi);
+    const float small = __fmaf_rn(c.x, d.lo, __fmaf_rn(c.y, d.hi, __fmaf_rn(c.x, d.hi, -p)));
+    const Pair t = two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, small));
+}
 
 }  // namespace heat
 
@@ -273,12 +312,11 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const Swe
     const int *__restrict__ rowcls = A.rowcls;
     const int *__restrict__ colcls = A.colcls;
     const LineTab<real> &R = A.R, &Z = A.Z;
-    const LineTab64 &R64 = A.R64, &Z64 = A.Z64;
     const BcVals bc = A.bc;
     if ((int)blockIdx.x * (int)(blockDim.x / G) * band >= Nz) return;  // past this instance (block-uniform)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ real sA[32], sB[32], sC[32];
-    __shared__ double sLo[32], sHi[32];
+    __shared__ real sLo[32], sHi[32];
     const int tid = threadIdx.x;
     const int g = tid % G;
     const int slot = tid / G;
@@ -437,55 +475,59 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 3 : 1) rsweep_kernel(const Swe
             }
         }
         if constexpr (MODE == MODE_REFINE) {
+            static_assert(sizeof(real) == 4, "the refined path is FP32");
             real dl0[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) dl0[k] = d[k];
             solve_row<real, K>(dl0, inv, f, cp, ls, W, lane, warp, nwl, wide, sA, sB, sC);
-            // FP64 residual of the increment system at delta = dl0
-            double xl = __shfl_up_sync(HEAT_FULL_MASK, (double)dl0[K - 1], 1, W);
-            double xr = __shfl_down_sync(HEAT_FULL_MASK, (double)dl0[0], 1, W);
+            // residual of the increment system at delta = dl0, from the FP64
+            // coefficients (as FP32 pairs) with exact differences and products
+            real xl = __shfl_up_sync(HEAT_FULL_MASK, dl0[K - 1], 1, W);
+            real xr = __shfl_down_sync(HEAT_FULL_MASK, dl0[0], 1, W);
             if (wide) {
                 __syncthreads();
-                if (lane == 0) sLo[warp] = (double)dl0[0];
-                if (lane == 31) sHi[warp] = (double)dl0[K - 1];
+                if (lane == 0) sLo[warp] = dl0[0];
+                if (lane == 31) sHi[warp] = dl0[K - 1];
                 __syncthreads();
-                if (lane == 0) xl = warp > 0 ? sHi[warp - 1] : 0.0;
-                if (lane == 31) xr = warp < nwl - 1 ? sLo[warp + 1] : 0.0;
+                if (lane == 0) xl = warp > 0 ? sHi[warp - 1] : real(0);
+                if (lane == 31) xr = warp < nwl - 1 ? sLo[warp + 1] : real(0);
             } else {
-                if (ls == 0) xl = 0.0;
-                if (ls == W - 1) xr = 0.0;
+                if (ls == 0) xl = real(0);
+                if (ls == W - 1) xr = real(0);
             }
-            const double tl64 = (double)nbl;
-            const double tr64 = (double)nbr;
+            const LineTab2 &R2 = A.R2, &Z2 = A.Z2;
             const size_t ro = (size_t)acls * Nr;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int i = i0 + k;
-                double rho = 0.0;
+                real rho = real(0);
                 if (valid && i < Nr) {
                     const size_t zo = (size_t)zc[k] * Nz + j;
-                    const double t0 = (double)tc[k];
-                    const double tl = k > 0 ? (double)tc[k - 1] : tl64;
-                    const double tr = k < K - 1 ? (double)tc[k + 1] : tr64;
-                    double r = R64.q[ro + i];
-                    r = fma(R64.am[ro + i], tl - t0, r);
-                    r = fma(R64.ap[ro + i], tr - t0, r);
-                    r = fma(R64.dl[ro + i], bc.th[0] - t0, r);
-                    r = fma(R64.dh[ro + i], bc.th[1] - t0, r);
-                    r = fma(Z64.am[zo], (double)tmv[k] - t0, r);
-                    r = fma(Z64.ap[zo], (double)tpv[k] - t0, r);
-                    r = fma(Z64.dl[zo], bc.th[2] - t0, r);
-                    r = fma(Z64.dh[zo], bc.th[3] - t0, r);
-                    const double xm = k > 0 ? (double)dl0[k - 1] : xl;
-                    const double xp = k < K - 1 ? (double)dl0[k + 1] : xr;
-                    const double Ax = R64.b[ro + i] * (double)dl0[k] - R64.m[ro + i] * xm - R64.p[ro + i] * xp;
-                    rho = r - Ax;
+                    const real t0 = tc[k];
+                    const real tl = k > 0 ? tc[k - 1] : nbl;
+                    const real tr = k < K - 1 ? tc[k + 1] : nbr;
+                    const float2 q2 = R2.q[ro + i];
+                    Pair acc{q2.x, q2.y};
+                    pair_add_cdiff(acc, R2.am[ro + i], tl, t0);
+                    pair_add_cdiff(acc, R2.ap[ro + i], tr, t0);
+                    if (i == 0) pair_add_cdiff(acc, R2.dl[ro + i], bc0, t0);
+                    if (i == Nr - 1) pair_add_cdiff(acc, R2.dh[ro + i], bc1, t0);
+                    pair_add_cdiff(acc, Z2.am[zo], tmv[k], t0);
+                    pair_add_cdiff(acc, Z2.ap[zo], tpv[k], t0);
+                    if (j == 0) pair_add_cdiff(acc, Z2.dl[zo], bc2, t0);
+                    if (j == Nz - 1) pair_add_cdiff(acc, Z2.dh[zo], bc3, t0);
+                    const real xm = k > 0 ? dl0[k - 1] : xl;
+                    const real xp = k < K - 1 ? dl0[k + 1] : xr;
+                    pair_add_cx(acc, R2.b[ro + i], -dl0[k]);
+                    pair_add_cx(acc, R2.m[ro + i], xm);
+                    pair_add_cx(acc, R2.p[ro + i], xp);
+                    rho = __fadd_rn(acc.hi, acc.lo);
                 }
-                d[k] = (real)rho;
+                d[k] = rho;
             }
             solve_row<real, K>(d, inv, f, cp, ls, W, lane, warp, nwl, wide, sA, sB, sC);
 #pragma unroll
-            for (int k = 0; k < K; ++k) d[k] = (real)((double)dl0[k] + (double)d[k]);
+            for (int k = 0; k < K; ++k) d[k] = dl0[k] + d[k];
         } else {
             solve_row<real, K>(d, inv, f, cp, ls, W, lane, warp, nwl, wide, sA, sB, sC);
         }
@@ -949,7 +991,6 @@ __global__ void __launch_bounds__(64, 8) zsolve_kernel(const SweepArgs<real> *__
     const real *__restrict__ pkA = A.pkA;
     const real *__restrict__ pkB = A.pkB;
     const LineTab<real> &R = A.R;
-    const LineTab64 &R64 = A.R64, &Z64 = A.Z64;
     const BcVals bc = A.bc;
     const real *__restrict__ zc = A.zc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1024,73 +1065,62 @@ __global__ void __launch_bounds__(64, 8) zsolve_kernel(const SweepArgs<real> *__
     }
 
     if constexpr (MODE == MODE_REFINE) {
-        // FP64 residual of the increment system at the FP32 solution x (now in
-        // shared memory); outside the chunk: x_{j0-1} = D_{c-1} + cp_{j0-1} x_{j0}
-        // and x_{j1} = X_{c+1}.
+        static_assert(sizeof(real) == 4, "the refined path is FP32");
+        // residual of the increment system at the FP32 solution x (now in
+        // shared memory), from the FP64 coefficients as FP32 pairs with exact
+        // differences and products; outside the chunk:
+        // x_{j0-1} = D_{c-1} + cp_{j0-1} x_{j0} and x_{j1} = X_{c+1}.
+        const LineTab2 &R2 = A.R2, &Z2 = A.Z2;
         const int ib = L.ib;
-        double xlo[V], xhi[V];
+        real xlo[V], xhi[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const bool in = ib + q < Nr;
             const real x0 = dsm[q];
-            xlo[q] = (j0 > 0 && in) ? (double)cin[q] + (double)L.pa[q][4 * (j0 - 1) + 2] * (double)x0 : 0.0;
-            xhi[q] = (j1 < Nz && in) ? (double)zc[((size_t)c * 2 + 1) * Nr + ib + q] : 0.0;
+            xlo[q] = (j0 > 0 && in) ? fmad(L.pa[q][4 * (j0 - 1) + 2], x0, cin[q]) : real(0);
+            xhi[q] = (j1 < Nz && in) ? zc[((size_t)c * 2 + 1) * Nr + ib + q] : real(0);
         }
-        double tm[V], t[V], tp[V];
-        {
-            real a0[V], a1[V];
-            L.row(th, j0 - 1, a0);
-            L.row(th, j0, a1);
+        real tm[V], t[V], tp[V];
+        L.row(th, j0 - 1, tm);
+        L.row(th, j0, t);
+        int a2 = -1;
+        float2 A0[V], A1[V];
 #pragma unroll
-            for (int q = 0; q < V; ++q) tm[q] = (double)a0[q], t[q] = (double)a1[q];
-        }
-        int a64 = -1;
-        double A0[V], A1[V];
-#pragma unroll
-        for (int q = 0; q < V; ++q) A0[q] = A1[q] = 0.0;
+        for (int q = 0; q < V; ++q) A0[q] = A1[q] = make_float2(0.f, 0.f);
         for (int j = j0; j < j1; ++j) {
-            {
-                real a2[V];
-                L.row(th, j + 1, a2);
-#pragma unroll
-                for (int q = 0; q < V; ++q) tp[q] = (double)a2[q];
-            }
-            real tlr, trr;
-            {
-                real tt[V];
-#pragma unroll
-                for (int q = 0; q < V; ++q) tt[q] = (real)t[q];
-                L.halo(j, tt, tlr, trr);
-            }
-            const double tl = (double)tlr, tr = (double)trr;
+            L.row(th, j + 1, tp);
+            real tl, tr;
+            L.halo(j, t, tl, tr);
             const int a = rowcls[j];
-            if (a != a64) {
-                a64 = a;
+            if (a != a2) {
+                a2 = a;
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
                     const int i = ib + q;
                     const size_t ro = (size_t)a * Nr + i;
-                    A0[q] = i < Nr ? (i == 0 ? R64.dl[ro] : R64.am[ro]) : 0.0;
-                    A1[q] = i < Nr ? (i == Nr - 1 ? R64.dh[ro] : R64.ap[ro]) : 0.0;
+                    A0[q] = i < Nr ? (i == 0 ? R2.dl[ro] : R2.am[ro]) : make_float2(0.f, 0.f);
+                    A1[q] = i < Nr ? (i == Nr - 1 ? R2.dh[ro] : R2.ap[ro]) : make_float2(0.f, 0.f);
                 }
             }
             real rr[V];
+            const real *xs = dsm + (size_t)(j - j0) * COLS;
 #pragma unroll
             for (int q = 0; q < V; ++q) {
                 const size_t zj = (size_t)L.b[q] * Nz + j;
-                const double l = q > 0 ? t[q - 1] : tl;
-                const double r = q < V - 1 ? t[q + 1] : tr;
-                const double zm = j == 0 ? Z64.dl[zj] : Z64.am[zj];
-                const double zp = j == Nz - 1 ? Z64.dh[zj] : Z64.ap[zj];
-                double v = Z64.q[zj];
-                v = fma(zm, tm[q] - t[q], v);
-                v = fma(zp, tp[q] - t[q], v);
-                v = fma(A0[q], l - t[q], v);
-                v = fma(A1[q], r - t[q], v);
-                const real *xs = dsm + (size_t)(j - j0) * COLS;
-                const double xm = j > j0 ? (double)xs[q - COLS] : xlo[q];
-                const double xp = j + 1 < j1 ? (double)xs[q + COLS] : xhi[q];
-                rr[q] = (real)(v - (Z64.b[zj] * (double)xs[q] - Z64.m[zj] * xm - Z64.p[zj] * xp));
+                const real l = q > 0 ? t[q - 1] : tl;
+                const real r = q < V - 1 ? t[q + 1] : tr;
+                const float2 q2 = Z2.q[zj];
+                Pair acc{q2.x, q2.y};
+                pair_add_cdiff(acc, j == 0 ? Z2.dl[zj] : Z2.am[zj], tm[q], t[q]);
+                pair_add_cdiff(acc, j == Nz - 1 ? Z2.dh[zj] : Z2.ap[zj], tp[q], t[q]);
+                pair_add_cdiff(acc, A0[q], l, t[q]);
+                pair_add_cdiff(acc, A1[q], r, t[q]);
+                const real xm = j > j0 ? xs[q - COLS] : xlo[q];
+                const real xp = j + 1 < j1 ? xs[q + COLS] : xhi[q];
+                pair_add_cx(acc, Z2.b[zj], -xs[q]);
+                pair_add_cx(acc, Z2.m[zj], xm);
+                pair_add_cx(acc, Z2.p[zj], xp);
+                rr[q] = __fadd_rn(acc.hi, acc.lo);
             }
             if (L.any) {
                 real *row = rho_out + (size_t)j * Nr + ib;

@@ -52,6 +52,8 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
     a.colcls = ctx->d_colcls;
     a.R64 = ctx->dR.full;
     a.Z64 = ctx->dZ.full;
+    a.R2 = ctx->dR.t2;
+    a.Z2 = ctx->dZ.t2;
     for (int f = 0; f < 4; ++f) a.bc.th[f] = ctx->theta_bc[f];
     a.ucls = ctx->zp.ucls;
     a.ztile = ctx->zp.tiles;
