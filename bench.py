@@ -311,7 +311,9 @@ def time_full_method(window_steps=None):
             "iterations_per_half_step": its / (2 * st["steps"]), "wall_s": w, "steps_per_s": st["steps"] / w,
             "cell_steps_per_s": cells * st["steps"] / w, "cell_iterations_per_s": cells * its / w,
             "launches": launches, "finite": bool(np.isfinite(T).all()),
-            "bound": "latency: one thread per line (100 r-lines of 1210 cells), a host read per iteration batch"}
+            "stored_cells": 80 * 1210 + 20 * 800,
+            "bound": "latency: 100 r-lines and 1210 z-lines of FP64 line solves per iteration, a host read of the "
+                     "convergence slots per batch of iterations"}
 
 
 def step_roofline(cells_active, word, ms_per_step):

@@ -317,11 +317,18 @@ typedef struct {
 } heat_nl_stats;
 
 /* Grid, regions and tables; T = T_init, time 0.  Errors: HEAT_ERR_ARG (bad
- * geometry as heat_create, Nr > HEAT_NL_MAX_NR, non-increasing knots, k or
- * C <= 0, bad options), HEAT_ERR_OOM, HEAT_ERR_CUDA.  On error *out is NULL.
- * Limit: an r-line is assembled and solved in one warp's shared memory (five
- * rows of Nr doubles), so Nr <= HEAT_NL_MAX_NR. */
-#define HEAT_NL_MAX_NR 5632
+ * geometry as heat_create, Nr or Nz > HEAT_NL_MAX_N, no active cell,
+ * non-increasing knots, k or C <= 0, bad options), HEAT_ERR_OOM,
+ * HEAT_ERR_CUDA.  On error *out is NULL.
+ * Layout (Sec. 3, eq. "grid": row j has N_j cells, column i has M_i): the
+ * field is stored without void padding, row j up to its last active cell
+ * (N_j = that cell's i + 1; void cells before it are kept as identity rows),
+ * and a column-packed copy likewise for the z-sweep.  Void cells past the
+ * last active cell of their row are not stored: heat_nl_field reports T_init
+ * there and heat_nl_set_field ignores them.
+ * Limit: a line is assembled and solved in one block's shared memory (five
+ * rows of doubles), so Nr, Nz <= HEAT_NL_MAX_N. */
+#define HEAT_NL_MAX_N 5632
 int heat_nl_create(const heat_geometry *geom, const heat_nl_materials *mat, const heat_pulse *pulse,
                    const heat_nl_options *opt, void *stream, heat_nl **out);
 
@@ -345,6 +352,12 @@ int heat_nl_half_field(heat_nl *s, double *out, size_t n, int on_device);
 int heat_nl_set_field(heat_nl *s, const double *in, size_t n, int on_device);
 /* Grid size and the number of kernel launches so far. */
 int heat_nl_info(heat_nl *s, int *Nr, int *Nz, long long *launches);
+/* The packed layout: N_j (Nz ints), M_i (Nr ints) and the stored cell count
+ * sum_j N_j (any pointer may be NULL). */
+int heat_nl_layout(heat_nl *s, int *N_j, int *M_i, long long *stored);
+/* The current field in the row-packed layout: n = sum_j N_j doubles, row j at
+ * offset sum_{j' < j} N_j', cells i = 0 .. N_j - 1.  on_device as heat_field. */
+int heat_nl_field_packed(heat_nl *s, double *out, size_t n, int on_device);
 void heat_nl_destroy(heat_nl *s);
 
 const char *heat_strerror(int status);

@@ -27,7 +27,8 @@ SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field"
            "heat_batch_tune", "heat_batch_set_tuning", "heat_batch_get_tuning", "heat_batch_launches_per_step",
            "heat_batch_destroy", "heat_batch_set_dt",
            "heat_nl_create", "heat_nl_step", "heat_nl_advance", "heat_nl_time", "heat_nl_set_time", "heat_nl_field",
-           "heat_nl_half_field", "heat_nl_set_field", "heat_nl_info", "heat_nl_destroy"]
+           "heat_nl_half_field", "heat_nl_set_field", "heat_nl_info", "heat_nl_destroy", "heat_nl_layout",
+           "heat_nl_field_packed"]
 
 
 class HeatError(RuntimeError):
@@ -129,6 +130,8 @@ def load():
         L.heat_nl_half_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.heat_nl_set_field.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.heat_nl_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_nl_layout.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_nl_field_packed.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.heat_nl_destroy.argtypes = [vp]
         L.heat_nl_destroy.restype = None
         _lib = L
@@ -463,3 +466,20 @@ class HeatNl:
         n = ctypes.c_longlong()
         _check("heat_nl_info", load().heat_nl_info(self._h, None, None, ctypes.byref(n)))
         return n.value
+
+    def layout(self):
+        """(N_j per row, M_i per column, stored cells) of the packed layout."""
+        Nj = np.zeros(self.Nz, dtype=np.int32)
+        Mi = np.zeros(self.Nr, dtype=np.int32)
+        n = ctypes.c_longlong()
+        _check("heat_nl_layout", load().heat_nl_layout(self._h, Nj.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                       Mi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                       ctypes.byref(n)))
+        return Nj, Mi, n.value
+
+    def field_packed(self):
+        """The field in the row-packed layout (row j: its N_j cells)."""
+        _, _, n = self.layout()
+        out = np.empty(n)
+        _check("heat_nl_field_packed", load().heat_nl_field_packed(self._h, out.ctypes.data_as(ctypes.c_void_p), n, 0))
+        return out

@@ -199,3 +199,49 @@ def test_full_method_arguments_rejected_without_gpu():
         assert st == -1 and h.value is None, (kw, st)
     assert L.heat_nl_step(None, 1.0, None, None) == -1
     assert L.heat_nl_advance(None, 1.0, 1, None) == -1
+
+
+@pytest.mark.gpu
+def test_paper_grid_is_stored_without_void_padding(gpu):
+    """Sec. 3, eq. "grid": the paper's example has N_j = 1210 cells in the 80
+    rows below z0 = 4 and 800 (the core) in the 20 rows above, M_i = 100 in
+    the 800 core columns and 80 in the others.  The full method stores
+    exactly those 112,800 cells (not 1210 x 100 = 121,000), and its packed
+    field is the rectangular field's stored cells, row by row."""
+    from paper_1912_03744_gb300 import HeatNl
+    p, m = H.paper_example_nl()
+    s = HeatNl(p, m, eps=1e-9, s_max=20, tau_base=m.t_src / 100, tau_trs=m.t_trs / 1000)
+    Nj, Mi, n = s.layout()
+    assert (Nj[:80] == 1210).all() and (Nj[80:] == 800).all()
+    assert (Mi[:800] == 100).all() and (Mi[800:] == 80).all()
+    assert n == 80 * 1210 + 20 * 800 == 112800
+    s.advance(3 * m.t_trs / 1000)
+    T, Tp = s.field(), s.field_packed()
+    np.testing.assert_array_equal(Tp, np.concatenate([T[j, :Nj[j]] for j in range(p.Nz)]))
+    assert (T[80:, 800:] == p.T_init).all()  # not stored: reported as T_init
+    s.close()
+
+
+@pytest.mark.gpu
+def test_layout_with_void_inside_lines(gpu):
+    """The five-region cell with its terminal cap: the columns past the core
+    have void cells between z = 8 and the cap (kept as identity rows inside
+    the column), the rows between z = 8 and 10 end at the core.  Parity with
+    the oracle on a ragged grid and the stored count."""
+    p = H.cell_problem(45, 61, H.config1().k, H.config1().C, 2e5, name="nl_cell")
+    m = _cell_laws(p)
+    s, o = _pair(p, m, eps=1e-8, s_max=30)
+    reg = o.grid()["region"]
+    Nj, Mi, n = s.layout()
+    want_Nj = np.array([np.max(np.nonzero(reg[j] >= 0)[0]) + 1 for j in range(p.Nz)])
+    want_Mi = np.array([np.max(np.nonzero(reg[:, i] >= 0)[0]) + 1 for i in range(p.Nr)])
+    np.testing.assert_array_equal(Nj, want_Nj)
+    np.testing.assert_array_equal(Mi, want_Mi)
+    assert n == want_Nj.sum() < p.Nr * p.Nz
+    tau = 20.0 * Oracle(p).tau_exp()
+    for k in range(4):
+        it = s.step(tau)
+        ok, i1, i2 = o.nl_step(k * tau, tau, 1e-8, 30)
+        assert ok and it == (i1, i2)
+    assert _rel(s.field(), o.field()) <= TOL
+    s.close()
