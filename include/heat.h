@@ -182,11 +182,30 @@ int heat_energy_noalloc(heat_ctx *ctx, double *E, double *Phi, double *Q);
 int heat_info(heat_ctx *ctx, int *Nr, int *Nz, double *r_centres, double *z_centres,
               double *tau_exp);
 
+/* The r-sweep kernel of a single context: kind 0 = the default rule; 1 =
+ * line teams (a warp walks each r-line in segments); 2 = register-resident
+ * lines (FP32 increment form, lines up to 2048 cells); 3 = walked lines (FP32
+ * increment form, rows a multiple of 4 cells up to 2080, staged by bulk copies,
+ * one warp per row); 4, 8, 16, 32 = block lines with kind cells per thread.
+ * HEAT_ERR_ARG (and the schedule unchanged) when the kind is not available
+ * for this context.  heat_get_rsweep returns the kind in use.  Synchronizes. */
+int heat_set_rsweep(heat_ctx *ctx, int kind);
+int heat_get_rsweep(heat_ctx *ctx);
+
 /* Number of kernel launches heat_step(ctx, 1) enqueues (for launch accounting). */
 int heat_launches_per_step(heat_ctx *ctx);
 
-/* Wait for the context stream; returns the first deferred error, if any. */
+/* Wait for the context stream; returns the first deferred error, if any, or
+ * HEAT_ERR_TIMEOUT when a kernel's bounded wait gave up since the last call
+ * (the kernel then skipped its work; the context stays usable). */
 int heat_sync(heat_ctx *ctx);
+
+/* Failure-detection test hook: with on = 1, the walked r-sweep (heat_set_rsweep
+ * kind 3, the one that stages rows by bulk copies on mbarriers) first waits,
+ * with a 2 ms limit, on a barrier nothing completes, records the time-out and
+ * skips the sweep; heat_sync then returns HEAT_ERR_TIMEOUT.  on = 0 restores
+ * normal operation.  No GPU fault is involved.  Synchronizes. */
+int heat_test_stall(heat_ctx *ctx, int on);
 
 void heat_destroy(heat_ctx *ctx);
 

@@ -218,6 +218,46 @@ int upload_rline(heat_ctx *ctx)
     return HEAT_OK;
 }
 
+// Walk r-sweep tables (FP32 increment form, one instance): lines whose rows
+// are 16-byte multiples (bulk copies) of at most 32 x 65 cells, at most 32
+// column classes.  Lane l, step k holds cell i = l K + k (K the smallest of
+// 17, 33, 65 with 32 K >= Nr); cells past Nr get zeros.
+int upload_rwalk(heat_ctx *ctx)
+{
+    ctx->rw_K = 0;
+    if (ctx->precision != HEAT_FP32) return HEAT_OK;
+    const int Nr = ctx->g.Nr;
+    if (Nr % 4 != 0 || Nr > 32 * 65 || ctx->Z.n_class > 32) return HEAT_OK;
+    const int K = Nr <= 32 * 17 ? 17 : (Nr <= 32 * 33 ? 33 : 65);
+    const int ncls = ctx->R.n_class;
+    const size_t per = (size_t)32 * K;
+    std::vector<float4> tab(per * ncls, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<signed char> cc(per, 0);
+    for (int a = 0; a < ncls; ++a)
+        for (int l = 0; l < 32; ++l)
+            for (int k = 0; k < K; ++k) {
+                const int i = l * K + k;
+                if (i >= Nr) continue;
+                const size_t ro = (size_t)a * Nr + i;
+                const double iv = ctx->R.inv[ro];
+                tab[a * per + (size_t)k * 32 + l] =
+                    make_float4((float)(ctx->R.xm[ro] * iv), (float)(ctx->R.xp[ro] * iv), (float)(ctx->R.q[ro] * iv),
+                                (float)iv);
+                if (a == 0) cc[(size_t)k * 32 + l] = (signed char)ctx->g.colcls[i];
+            }
+    if (ctx->d_rwtab) cudaFree(ctx->d_rwtab), ctx->d_rwtab = nullptr;
+    if (ctx->d_rwcc) cudaFree(ctx->d_rwcc), ctx->d_rwcc = nullptr;
+    HEAT_CHECK(cudaMalloc(&ctx->d_rwtab, tab.size() * sizeof(float4)));
+    HEAT_CHECK(cudaMalloc(&ctx->d_rwcc, cc.size()));
+    HEAT_CHECK(cudaMemcpyAsync(ctx->d_rwtab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    HEAT_CHECK(cudaMemcpyAsync(ctx->d_rwcc, cc.data(), cc.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->rw_K = K;
+    ctx->rw_ncc = ctx->Z.n_class;
+    return HEAT_OK;
+}
+
 void free_ctx(heat_ctx *ctx)
 {
     if (!ctx) return;
@@ -225,7 +265,8 @@ void free_ctx(heat_ctx *ctx)
                     ctx->d_colcls, ctx->d_wr,       ctx->d_wz,       ctx->d_field[0], ctx->d_field[1],
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
                     ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,
-                    ctx->d_args,   ctx->d_rl,       ctx->d_rlz,      ctx->zp.tiles};
+                    ctx->d_args,   ctx->d_rl,       ctx->d_rlz,      ctx->zp.tiles, ctx->d_rwtab, ctx->d_rwcc,
+                    ctx->d_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -249,6 +290,7 @@ int ctx_set_dt(heat_ctx *ctx, double dt)
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return st;
     if ((st = upload_zpart(ctx)) != HEAT_OK) return st;
     if ((st = upload_rline(ctx)) != HEAT_OK) return st;
+    if ((st = upload_rwalk(ctx)) != HEAT_OK) return st;
     return cuda_status(ctx_plan(ctx));
 }
 }  // namespace heat
@@ -318,6 +360,7 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     if ((st = upload_tab(ctx, ctx->Z, ctx->dZ)) != HEAT_OK) return fail(st);
     if ((st = upload_zpart(ctx)) != HEAT_OK) return fail(st);
     if ((st = upload_rline(ctx)) != HEAT_OK) return fail(st);
+    if ((st = upload_rwalk(ctx)) != HEAT_OK) return fail(st);
     std::vector<double> wr(g.Nr), wz(g.Nz);
     for (int i = 0; i < g.Nr; ++i) wr[i] = 2.0 * kPi * g.rc[i] * g.hbar[i];
     for (int j = 0; j < g.Nz; ++j) wz[j] = g.etabar[j];
@@ -333,6 +376,8 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     ctx->n_part = energy_blocks(ctx);
     HEAT_TRY(cudaMalloc(&ctx->d_part, 2 * ctx->n_part * sizeof(double)));
     HEAT_TRY(cudaMalloc(&ctx->d_res, 2 * sizeof(double)));
+    HEAT_TRY(cudaMalloc(&ctx->d_status, sizeof(int)));
+    HEAT_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     if (ctx->precision == HEAT_FP32_REFINED) HEAT_TRY(cudaMalloc(&ctx->d_rho, ncell * sizeof(float)));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_rowcls, g.rowcls.data(), g.Nz * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HEAT_TRY(cudaMemcpyAsync(ctx->d_colcls, g.colcls.data(), g.Nr * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -447,7 +492,42 @@ int heat_sync(heat_ctx *ctx)
 {
     if (!ctx) return HEAT_ERR_ARG;
     HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    int status = 0;
+    HEAT_CHECK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        HEAT_CHECK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        return HEAT_ERR_TIMEOUT;
+    }
     return ctx->deferred;
+}
+
+int heat_set_rsweep(heat_ctx *ctx, int kind)
+{
+    if (!ctx || ctx->batch_member || kind < 0 || kind > 32) return HEAT_ERR_ARG;
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    const int old = ctx->rsweep_req;
+    ctx->rsweep_req = kind;
+    const cudaError_t e = ctx_plan(ctx);
+    if (e == cudaErrorInvalidValue) {  // not available for this context: keep the previous schedule
+        ctx->rsweep_req = old;
+        const cudaError_t e2 = ctx_plan(ctx);
+        return e2 == cudaSuccess ? HEAT_ERR_ARG : cuda_status(e2);
+    }
+    return cuda_status(e);
+}
+
+int heat_get_rsweep(heat_ctx *ctx)
+{
+    if (!ctx) return HEAT_ERR_ARG;
+    return ctx->plan.used.rK;
+}
+
+int heat_test_stall(heat_ctx *ctx, int on)
+{
+    if (!ctx || ctx->batch_member) return HEAT_ERR_ARG;
+    HEAT_CHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->rw_stall = on ? 1 : 0;
+    return cuda_status(ctx_plan(ctx));
 }
 
 void heat_destroy(heat_ctx *ctx)

@@ -137,6 +137,14 @@ struct SweepArgs {
                               // stride of a warp's shared-memory slice: a block mixes instances)
     real *zs, *zc, *rho;
     real *f0, *f1;
+    // walk r-sweep (FP32 increment form, heat_rwalk.cuh): per row class the
+    // coefficients {f, cp, q inv, inv} of cell l K + k at [class][k][lane],
+    // the column class of each cell at [k][lane], the number of column classes
+    const float4 *rw_tab;
+    const signed char *rw_cc;
+    int rw_K, rw_ncc;
+    int rw_stall;             // failure-detection test: the walk's first wait runs out
+    int *status;              // device status word: bit 0 = a bounded wait gave up
 };
 
 // One kernel launch of a sweep.  Every sweep kernel takes a device array of
@@ -282,4 +290,11 @@ struct heat_ctx {
     std::vector<unsigned char> h_args;  // one SweepArgs<real>
     void *d_args = nullptr;
     bool batch_member = false;          // owned by a heat_batch (no heat_sweep / heat_destroy)
+    // walk r-sweep tables (FP32 increment form; rw_K = 0 when not built)
+    void *d_rwtab = nullptr;
+    signed char *d_rwcc = nullptr;
+    int rw_K = 0, rw_ncc = 0;
+    int rw_stall = 0;
+    int *d_status = nullptr;            // bit 0: a kernel's bounded wait gave up
+    int rsweep_req = 0;                 // requested r-sweep kernel (heat_set_rsweep; 0 = default rule)
 };

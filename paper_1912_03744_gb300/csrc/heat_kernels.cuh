@@ -98,6 +98,7 @@ __device__ __forceinline__ void pair_add_cdiff(Pair &acc, float2 c, float u, flo
 
 #include "heat_rline.cuh"
 #include "heat_rblock.cuh"
+#include "heat_rwalk.cuh"
 #include "heat_zline.cuh"
 
 namespace heat {
@@ -1461,6 +1462,44 @@ static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L
     return cudaSuccess;
 }
 
+// Walk r-sweep (heat_rwalk.cuh) for one FP32 instance with its tables
+// built (rw_K > 0): a band of rows per block, a multiple of the block's 4
+// rows, one block per SM.
+template <int K>
+static cudaError_t plan_rwalk_k(SweepArgs<float> *h, Tuning &tu, Launch &L)
+{
+    const void *fn = (const void *)rwalk_kernel<K>;
+    const size_t smem = RwLayout<K>::bytes;
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kRwWarps, smem)) != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const int groups = (h[0].Nz + kRwWarps - 1) / kRwWarps;
+    const int per_block = (groups + kSMs * per_sm - 1) / (kSMs * per_sm);
+    h[0].band = per_block * kRwWarps;
+    h[0].G = 32;
+    tu.band = h[0].band;
+    tu.rK = 3;
+    L.fn = fn;
+    L.grid = dim3((h[0].Nz + h[0].band - 1) / h[0].band, 1, 1);
+    L.block = dim3(32 * kRwWarps, 1, 1);
+    L.smem = smem;
+    L.flip = true;
+    return cudaSuccess;
+}
+
+static cudaError_t plan_rwalk(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
+{
+    if (n != 1 || h[0].rw_K == 0 || h[0].rw_tab == nullptr) return cudaErrorInvalidValue;
+    switch (h[0].rw_K) {
+    case 17: return plan_rwalk_k<17>(h, tu, L);
+    case 33: return plan_rwalk_k<33>(h, tu, L);
+    case 65: return plan_rwalk_k<65>(h, tu, L);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename real, int MODE>
 static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
@@ -1578,14 +1617,21 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     bool line_tables = MODE == MODE_LIT || MODE == MODE_DELTA;
     for (int m = 0; m < n && line_tables; ++m) line_tables = h[m].rl.tA != nullptr;
     // rK: 0 = default, 1 = line teams, 2 = register-resident lines (FP32
-    // increment form), 4..32 = block lines with rK cells per thread
+    // increment form), 3 = walked lines (FP32 increment form, one instance),
+    // 4..32 = block lines with rK cells per thread
     if constexpr (MODE == MODE_DELTA && sizeof(real) == 4) {
-        if (tu.rK == 0 || tu.rK == 2) {
+        // walked lines on request only: measured slower than the register-
+        // resident lines on lines of 512 to 2048 cells
+        if (tu.rK == 3) {
+            e = plan_rwalk(h, n, tu, r);
+            if (e != cudaSuccess) return e;
+        }
+        if (e != cudaSuccess && (tu.rK == 0 || tu.rK == 2)) {
             e = plan_rblock(h, n, tu, r);
             if (e != cudaSuccess && tu.rK == 2) return e;
         }
     } else {
-        if (tu.rK == 2) return cudaErrorInvalidValue;
+        if (tu.rK == 2 || tu.rK == 3) return cudaErrorInvalidValue;
     }
     if constexpr (MODE == MODE_LIT || MODE == MODE_DELTA) {
         if (e == cudaErrorInvalidValue) {

@@ -77,6 +77,12 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
     }
     a.f0 = static_cast<real *>(ctx->d_field[0]);
     a.f1 = static_cast<real *>(ctx->d_field[1]);
+    a.rw_tab = static_cast<const float4 *>(ctx->d_rwtab);
+    a.rw_cc = ctx->d_rwcc;
+    a.rw_K = ctx->rw_K;
+    a.rw_ncc = ctx->rw_ncc;
+    a.rw_stall = ctx->rw_stall;
+    a.status = ctx->d_status;
     *static_cast<SweepArgs<real> *>(dst) = a;
 }
 
@@ -153,7 +159,9 @@ cudaError_t ctx_plan(heat_ctx *ctx)
 {
     ctx->h_args.assign(args_bytes(ctx->precision), 0);
     fill_args(ctx, ctx->h_args.data());
-    cudaError_t e = make_plan(ctx->precision, ctx->h_args.data(), 1, Tuning(), ctx->plan);
+    Tuning req;
+    req.rK = ctx->rsweep_req;
+    cudaError_t e = make_plan(ctx->precision, ctx->h_args.data(), 1, req, ctx->plan);
     if (e != cudaSuccess) return e;
     if (!ctx->d_args && (e = cudaMalloc(&ctx->d_args, ctx->h_args.size())) != cudaSuccess) return e;
     e = cudaMemcpyAsync(ctx->d_args, ctx->h_args.data(), ctx->h_args.size(), cudaMemcpyHostToDevice, ctx->stream);

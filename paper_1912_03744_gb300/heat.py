@@ -28,7 +28,7 @@ SYMBOLS = ["heat_create", "heat_set_dt", "heat_step", "heat_sweep", "heat_field"
            "heat_batch_destroy", "heat_batch_set_dt",
            "heat_nl_create", "heat_nl_step", "heat_nl_advance", "heat_nl_time", "heat_nl_set_time", "heat_nl_field",
            "heat_nl_half_field", "heat_nl_set_field", "heat_nl_info", "heat_nl_destroy", "heat_nl_layout",
-           "heat_nl_field_packed"]
+           "heat_nl_field_packed", "heat_test_stall", "heat_set_rsweep", "heat_get_rsweep"]
 
 
 class HeatError(RuntimeError):
@@ -104,6 +104,9 @@ def load():
         L.heat_info.argtypes = [vp, ip, ip, dp, dp, dp]
         L.heat_launches_per_step.argtypes = [vp]
         L.heat_sync.argtypes = [vp]
+        L.heat_test_stall.argtypes = [vp, ctypes.c_int]
+        L.heat_set_rsweep.argtypes = [vp, ctypes.c_int]
+        L.heat_get_rsweep.argtypes = [vp]
         L.heat_destroy.argtypes = [vp]
         L.heat_destroy.restype = None
         L.heat_strerror.argtypes = [ctypes.c_int]
@@ -272,6 +275,13 @@ class HeatSolver:
         _check("heat_info", load().heat_info(self._h, None, None, rc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                              zc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None))
         return rc, zc
+
+    def set_rsweep(self, kind: int):
+        """Choose the r-sweep kernel (include/heat.h, heat_set_rsweep)."""
+        _check("heat_set_rsweep", load().heat_set_rsweep(self._h, int(kind)))
+
+    def rsweep(self) -> int:
+        return int(load().heat_get_rsweep(self._h))
 
     def launches_per_step(self) -> int:
         return int(load().heat_launches_per_step(self._h))

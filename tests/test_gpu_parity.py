@@ -280,3 +280,30 @@ def test_config4_subsample_against_the_oracle(precision):
     assert rel <= 1e-5, rel
     assert rise <= 1e-5, rise
     assert derr <= 1e-5, derr
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 8, 16, 32])
+@pytest.mark.parametrize("shape", [(512, 300), (1024, 130), (2048, 37), (300, 70)])
+def test_every_rsweep_kernel_of_a_single_instance(kind, shape):
+    """Each r-sweep kernel heat_set_rsweep can pick (line teams, register-
+    resident lines, walked lines, block lines), on lines of 300 to 2048 cells
+    (300: not a multiple of 4, the walked lines decline), FP32, 6 steps."""
+    from paper_1912_03744_gb300.heat import HeatError
+    p = H.config2(*shape)
+    o = Oracle(p)
+    tau = H.DT_FACTOR * o.tau_exp()
+    s = _solver(p, tau, "fp32")
+    try:
+        s.set_rsweep(kind)
+    except HeatError:
+        assert kind == 3 and shape[0] % 4 != 0 or kind == 2 and shape[0] > 2048 or kind in (4,) and shape[0] > 4096
+        s.close()
+        return
+    assert s.rsweep() == kind
+    T0 = H.random_field(p, seed=kind + shape[0], amp=20.0)
+    s.set_field(T0)
+    o.set_field(T0)
+    s.step(6)
+    o.step(tau, 6)
+    assert _rel(s.field(), o.field()) <= TOL["fp32"]
+    s.close()

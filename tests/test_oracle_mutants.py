@@ -31,7 +31,8 @@ MUTANTS = {
     "transposed_offdiagonals": ("                a[i] = -o->Arm[c];\n                cc[i] = -o->Arp[c];",
                                 "                a[i] = -o->Arp[c];\n                cc[i] = -o->Arm[c];"),
     "thomas_pivot": ("dw[i] = (d[i] - a[i] * dw[i - 1]) / m;", "dw[i] = (d[i] - a[i] * dw[i - 1]) / b[i];"),
-    "full_tau_in_half_step": ("const double half = 0.5 * tau;", "const double half = tau;"),
+    "full_tau_in_half_step": ("const double half = 0.5 * tau;\n    double *T = o->T, *Tb = o->Tbar;",
+                              "const double half = tau;\n    double *T = o->T, *Tb = o->Tbar;"),
     "source_dropped_in_half_step_2": (
         "d[j] = w * Tb[c] + lambda_r(o, Tb, i, j) + xs + o->Dzl[c] * o->Tbc[2] + o->Dzh[c] * o->Tbc[3];",
         "d[j] = w * Tb[c] + lambda_r(o, Tb, i, j) + o->Dzl[c] * o->Tbc[2] + o->Dzh[c] * o->Tbc[3];"),

@@ -126,3 +126,39 @@ def test_nonfinite_field_is_reported_and_the_context_recovers(precision, value):
     s.step(2)
     assert np.isfinite(s.field()).all()
     s.close()
+
+
+@pytest.mark.gpu
+def test_bounded_wait_reports_a_timeout_and_the_context_recovers():
+    """The FP32 r-sweep that stages rows by bulk copies waits on mbarriers with
+    a time limit.  The test hook makes its first wait run out (a barrier
+    nothing completes, no copy issued): heat_sync must return
+    HEAT_ERR_TIMEOUT, and with the hook off the next steps must match the
+    oracle again."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import Oracle
+    from paper_1912_03744_gb300 import HeatSolver
+    from paper_1912_03744_gb300 import heat as hb
+    p = H.config2(256, 64)
+    o = Oracle(p)
+    tau = 20.0 * o.tau_exp()
+    s = HeatSolver(p, tau, precision="fp32")
+    s.set_rsweep(3)  # the r-sweep that stages rows by bulk copies on mbarriers
+    L = hb.load()
+    assert L.heat_test_stall(s._h, 1) == HEAT_OK
+    s.step(1)
+    assert L.heat_sync(s._h) == -4  # HEAT_ERR_TIMEOUT
+    assert L.heat_sync(s._h) == HEAT_OK  # reported once
+    assert L.heat_test_stall(s._h, 0) == HEAT_OK
+    T0 = H.random_field(p, seed=5, amp=10.0)
+    s.set_field(T0)
+    o.set_field(T0)
+    s.step(3)
+    o.step(tau, 3)
+    assert L.heat_sync(s._h) == HEAT_OK
+    assert float(np.max(np.abs(s.field() - o.field())) / np.max(np.abs(o.field()))) <= 1e-5
+    s.close()
