@@ -27,6 +27,8 @@ void set_zitems(int precision, void *h, int n, const void *items, int n_items);
 cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPlan &plan);
 cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s);
 int ctx_set_dt(heat_ctx *ctx, double dt);
+int create_ctx(const heat_geometry *, const heat_materials *, const heat_options *, double, void *, bool,
+               heat_ctx **);
 }  // namespace heat
 
 using namespace heat;
@@ -191,12 +193,11 @@ int heat_batch_create(int n, const heat_geometry *geoms, const heat_materials *m
     b->h_args.assign(ab * n, 0);
     for (int i = 0; i < n; ++i) {
         heat_ctx *c = nullptr;
-        int st = heat_create(&geoms[i], &mats[i], opt, dts[i], b->s, &c);
+        int st = create_ctx(&geoms[i], &mats[i], opt, dts[i], b->s, true, &c);
         if (st != HEAT_OK) {
             free_batch(b);
             return st;
         }
-        c->batch_member = true;
         b->m.push_back(c);
         fill_args(c, b->h_args.data() + ab * i);
     }

@@ -28,6 +28,8 @@ cudaError_t launch_theta_to_T(heat_ctx *, double *);
 cudaError_t launch_T_to_theta(heat_ctx *, const double *);
 int launches_per_step(const heat_ctx *);
 int energy_blocks(const heat_ctx *);
+int create_ctx(const heat_geometry *, const heat_materials *, const heat_options *, double, void *, bool,
+               heat_ctx **);
 }  // namespace heat
 
 using namespace heat;
@@ -315,12 +317,23 @@ const char *heat_strerror(int status)
 int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat_options *opt, double dt,
                 void *stream, heat_ctx **out)
 {
+    return heat::create_ctx(geom, mat, opt, dt, stream, false, out);
+}
+
+}  // extern "C"
+
+namespace heat {
+// heat_create, for a standalone context or (member = true) a batch member.
+int create_ctx(const heat_geometry *geom, const heat_materials *mat, const heat_options *opt, double dt,
+               void *stream, bool member, heat_ctx **out)
+{
     if (!out) return HEAT_ERR_ARG;
     *out = nullptr;
     int st = validate(geom, mat, opt, dt);
     if (st != HEAT_OK) return st;
     heat_ctx *ctx = new (std::nothrow) heat_ctx();
     if (!ctx) return HEAT_ERR_OOM;
+    ctx->batch_member = member;
     ctx->precision = opt->precision;
     ctx->face_mean = opt->face_mean;
     ctx->stream = static_cast<cudaStream_t>(stream);
@@ -392,7 +405,9 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
     *out = ctx;
     return HEAT_OK;
 }
+}  // namespace heat
 
+extern "C" {
 
 int heat_set_dt(heat_ctx *ctx, double dt)
 {

@@ -226,13 +226,24 @@ struct ZPart {
 std::vector<int> z_tiles(const std::vector<int> &colcls, int Nr, int V);
 
 // Rows per z chunk (one warp walks a chunk of its columns): 32, or more
-// (a multiple of 4) so that a column has at most 256 chunks.
-inline int z_chunk_rows(int, int Nz)
+// (a multiple of 4) so that a column has at most 256 chunks.  A single
+// instance whose z-sweep would then have fewer than two warps per SM (a small
+// grid: every warp walks its chunk alone on an SM, and in FP64 the SM's two
+// FP64 FMAs per clock bound it) takes chunks of 16 or 8 rows instead, as long
+// as a column stays within 256 chunks; batch members keep 32 (the batch's
+// work list spreads their warps already).
+inline int z_chunk_rows(int precision, int Nr, int Nz, bool spread)
 {
     if (Nz <= 32) return Nz;
     int rc = (Nz + 255) / 256;
     rc = (rc + 3) / 4 * 4;
-    return rc < 32 ? 32 : rc;
+    rc = rc < 32 ? 32 : rc;
+    if (spread && rc == 32) {
+        const int cols = precision == HEAT_FP64 ? 64 : 128;  // columns per warp (one 16-byte segment per lane)
+        const long long col_warps = (Nr + cols - 1) / cols;
+        while (rc > 8 && col_warps * ((Nz + rc - 1) / rc) < 2 * 152 && (Nz + rc / 2 - 1) / (rc / 2) <= 256) rc /= 2;
+    }
+    return rc;
 }
 // Columns per thread of the z-sweep (one 8- or 16-byte row segment).
 inline int z_cols_per_thread(int) { return 2; }

@@ -277,7 +277,7 @@ void build_zpartition(heat_ctx *ctx)
 {
     const HostTab &Z = ctx->Z;
     const int Nz = Z.N, nb = Z.n_class;
-    const int Rc = z_chunk_rows(ctx->precision, Nz);
+    const int Rc = z_chunk_rows(ctx->precision, ctx->g.Nr, Nz, !ctx->batch_member);
     const int nch = (Nz + Rc - 1) / Rc;
     ctx->zp.Rc = Rc;
     ctx->zp.n_chunks = nch;
