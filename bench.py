@@ -366,9 +366,10 @@ def time_ensemble(steps, warmup, precision="fp32", tuning=None):
     return out
 
 
-def time_config4(steps, warmup):
+def time_config4(steps, warmup, grid=(8192, 16384)):
     """Precision stress at full size: 8192 x 16384 (134 M cells), conductivity
-    contrast 1e4, FP32 line solves with the FP64 residual refinement; CUDA
+    contrast 1e4, FP32 line solves with the residual refinement (the residual
+    from the FP64 coefficients in extended precision); CUDA
     events around `steps` steps (each field is 537 MB, larger than L2), and
     the FP64 heat balance of one step measured by the library itself:
     E(next) - E(now) - tau Q - tau/2 (Phi(now) + Phi(next)), relative to the
@@ -376,7 +377,7 @@ def time_config4(steps, warmup):
     subsample test (tests/test_gpu_parity.py)."""
     import torch
     from paper_1912_03744_gb300 import HeatSolver
-    p = H.config4()
+    p = H.config4(*grid)
     probe = HeatSolver(p, 1.0, precision="fp32_refined")
     tau = H.DT_FACTOR * probe.tau_exp
     act = active_cells(probe, p)
@@ -398,7 +399,7 @@ def time_config4(steps, warmup):
         launches = s.launches_per_step()
         s.close()
     resid = (E1 - E0) - tau * Q - 0.5 * tau * (Phi0 + Phi1)
-    return {"workload": "config4: 8192x16384, k 0.04/400 (contrast 1e4), seed 4, dt=50*tau_exp",
+    return {"workload": f"config4: {p.Nr}x{p.Nz}, k 0.04/400 (contrast 1e4), seed 4, dt=50*tau_exp",
             "precision": "fp32_refined", "steps": steps, "ms_per_step": ms / steps,
             "cell_steps_per_s": act * steps / (ms * 1e-3), "active_cells": act,
             "heat_balance_rel": abs(resid) / abs(E1 - E0), "launches_per_step": launches,
@@ -557,6 +558,9 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=4096, help="solver runs the surrogate trains on")
     ap.add_argument("--surrogate-epochs", type=int, default=10)
     ap.add_argument("--config4-steps", type=int, default=20)
+    ap.add_argument("--config4-grid", default="8192,16384", help="Nr,Nz of the config-4 leg (profiling: smaller)")
+    ap.add_argument("--leg", default=None, choices=["config1", "config4", "ensemble", "surrogate", "full"],
+                    help="time one leg only and print it (for profiling)")
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=4096)
     args = ap.parse_args()
@@ -575,6 +579,15 @@ def main():
     __graft_entry__.build()
 
     ens_tuning = tuple(int(x) for x in args.ensemble_tuning.split(",")) if args.ensemble_tuning else None
+    if args.leg:
+        legs = {"config1": lambda: time_config1(),
+                "config4": lambda: time_config4(args.config4_steps, args.warmup,
+                                                tuple(int(x) for x in args.config4_grid.split(","))),
+                "ensemble": lambda: time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning),
+                "surrogate": lambda: time_surrogate(args.surrogate_train, args.surrogate_epochs),
+                "full": lambda: time_full_method()}
+        print(json.dumps({"leg": args.leg, **legs[args.leg]()}), flush=True)
+        return
     if args.ensemble_only:
         print(json.dumps({"ensemble_only": True, **time_ensemble(args.ensemble_steps, args.warmup,
                                                                  tuning=ens_tuning)}), flush=True)
