@@ -186,7 +186,11 @@ int heat_info(heat_ctx *ctx, int *Nr, int *Nz, double *r_centres, double *z_cent
  * line teams (a warp walks each r-line in segments); 2 = register-resident
  * lines (FP32 increment form, lines up to 2048 cells); 3 = walked lines (FP32
  * increment form, rows a multiple of 4 cells up to 2080, staged by bulk copies,
- * one warp per row); 4, 8, 16, 32 = block lines with kind cells per thread.
+ * one warp per row); 5 = cluster lines (both FP32 precisions, lines up to
+ * 16384 cells, a thread-block cluster of ceil(Nr / 2048) blocks per line,
+ * the default for FP32 lines longer than 2048 cells and for every refined
+ * FP32 context within that length); 4, 8, 16, 32 = block lines with kind
+ * cells per thread.
  * HEAT_ERR_ARG (and the schedule unchanged) when the kind is not available
  * for this context.  heat_get_rsweep returns the kind in use.  Synchronizes. */
 int heat_set_rsweep(heat_ctx *ctx, int kind);

@@ -154,6 +154,7 @@ struct Launch {
     dim3 grid, block;
     size_t smem = 0;
     bool flip = false;
+    int cluster = 1;  // blocks per thread-block cluster along x (1: no cluster)
 };
 
 // Launch schedule of both half-steps for one set of instances (one problem,

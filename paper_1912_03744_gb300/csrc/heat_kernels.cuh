@@ -99,6 +99,7 @@ __device__ __forceinline__ void pair_add_cdiff(Pair &acc, float2 c, float u, flo
 #include "heat_rline.cuh"
 #include "heat_rblock.cuh"
 #include "heat_rwalk.cuh"
+#include "heat_rclus.cuh"
 #include "heat_zline.cuh"
 
 namespace heat {
@@ -1271,6 +1272,7 @@ static cudaError_t plan_rsweep_k(SweepArgs<real> *h, int n, int band_req, Launch
         Gmax = h[m].G > Gmax ? h[m].G : Gmax;
     }
     if (n > 1 && Gmax > 32) return cudaErrorInvalidValue;
+    if (Gmax > 1024) return cudaErrorInvalidValue;  // a line longer than one block of K-cell threads
     const int block = Gmax <= 32 ? 128 : Gmax;
     // deepest ring that fits: 8 rows, else 4, else direct loads
     const size_t row_bytes = (size_t)block * K * sizeof(real);
@@ -1500,6 +1502,58 @@ static cudaError_t plan_rwalk(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
     }
 }
 
+// Cluster r-sweep (heat_rclus.cuh) for one FP32 instance in an increment
+// form: CL = ceil(Nr / 2048) blocks per line (at most 8), bands of rows
+// sized so that the clusters that fit on the device at once take one band
+// each.
+template <int MODE>
+static cudaError_t plan_rclus(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
+{
+    if (n != 1) return cudaErrorInvalidValue;
+    const int Nr = h[0].Nr, Nz = h[0].Nz;
+    const int CL = (Nr + kRcSeg - 1) / kRcSeg;
+    if (CL > kRcMaxCl) return cudaErrorInvalidValue;
+    if (MODE == MODE_REFINE && h[0].R2.q == nullptr) return cudaErrorInvalidValue;
+    const bool exact = Nr == CL * kRcSeg;
+    const void *fn = exact ? (const void *)rclus_kernel<MODE, true> : (const void *)rclus_kernel<MODE, false>;
+    const size_t smem = rc_smem_bytes<MODE>();
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int active = 0;
+    if (CL > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CL, 1, 1);
+        cfg.blockDim = dim3(kRcThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = (unsigned)CL;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        if ((e = cudaOccupancyMaxActiveClusters(&active, fn, &cfg)) != cudaSuccess) return e;
+    } else {
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRcThreads, smem)) != cudaSuccess) return e;
+        active = kSMs * per_sm;
+    }
+    if (active < 1) return cudaErrorInvalidValue;
+    int band = tu.band > 0 ? tu.band : (Nz + active - 1) / active;
+    band = band < 1 ? 1 : band;
+    h[0].G = CL * kRcThreads;
+    h[0].band = band;
+    tu.band = band;
+    tu.rK = 5;
+    L.fn = fn;
+    L.grid = dim3(CL * ((Nz + band - 1) / band), 1, 1);
+    L.block = dim3(kRcThreads, 1, 1);
+    L.smem = smem;
+    L.flip = true;
+    L.cluster = CL;
+    return cudaSuccess;
+}
+
 template <typename real, int MODE>
 static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
@@ -1618,7 +1672,8 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     for (int m = 0; m < n && line_tables; ++m) line_tables = h[m].rl.tA != nullptr;
     // rK: 0 = default, 1 = line teams, 2 = register-resident lines (FP32
     // increment form), 3 = walked lines (FP32 increment form, one instance),
-    // 4..32 = block lines with rK cells per thread
+    // 5 = cluster lines (FP32 increment forms, one instance), 4, 8, 16, 32 =
+    // block lines with rK cells per thread
     if constexpr (MODE == MODE_DELTA && sizeof(real) == 4) {
         // walked lines on request only: measured slower than the register-
         // resident lines on lines of 512 to 2048 cells
@@ -1630,8 +1685,27 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
             e = plan_rblock(h, n, tu, r);
             if (e != cudaSuccess && tu.rK == 2) return e;
         }
-    } else {
+        // lines longer than one block holds: a cluster per line
+        if (e != cudaSuccess && (tu.rK == 0 || tu.rK == 5)) {
+            e = plan_rclus<MODE>(h, n, tu, r);
+            if (e != cudaSuccess && tu.rK == 5) return e;
+            if (e != cudaSuccess) {  // not available: the next kernel in line
+                (void)cudaGetLastError();
+                e = cudaErrorInvalidValue;
+            }
+        }
+    } else if constexpr (MODE == MODE_REFINE) {
         if (tu.rK == 2 || tu.rK == 3) return cudaErrorInvalidValue;
+        if (tu.rK == 0 || tu.rK == 5) {
+            e = plan_rclus<MODE>(h, n, tu, r);
+            if (e != cudaSuccess && tu.rK == 5) return e;
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                e = cudaErrorInvalidValue;
+            }
+        }
+    } else {
+        if (tu.rK == 2 || tu.rK == 3 || tu.rK == 5) return cudaErrorInvalidValue;
     }
     if constexpr (MODE == MODE_LIT || MODE == MODE_DELTA) {
         if (e == cudaErrorInvalidValue) {

@@ -122,11 +122,18 @@ cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int fli
         cfg.blockDim = L.block;
         cfg.dynamicSmemBytes = L.smem;
         cfg.stream = s;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        if (L.cluster > 1) {
+            attr[1].id = cudaLaunchAttributeClusterDimension;
+            attr[1].val.clusterDim.x = (unsigned)L.cluster;
+            attr[1].val.clusterDim.y = 1;
+            attr[1].val.clusterDim.z = 1;
+            cfg.numAttrs = 2;
+        }
         cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, kargs);
         if (e != cudaSuccess) return e;
     }

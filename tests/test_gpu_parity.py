@@ -282,7 +282,7 @@ def test_config4_subsample_against_the_oracle(precision):
     assert derr <= 1e-5, derr
 
 
-@pytest.mark.parametrize("kind", [1, 2, 3, 4, 8, 16, 32])
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5, 8, 16, 32])
 @pytest.mark.parametrize("shape", [(512, 300), (1024, 130), (2048, 37), (300, 70)])
 def test_every_rsweep_kernel_of_a_single_instance(kind, shape):
     """Each r-sweep kernel heat_set_rsweep can pick (line teams, register-
