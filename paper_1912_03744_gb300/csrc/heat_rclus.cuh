@@ -344,97 +344,148 @@ __global__ void __launch_bounds__(kRcThreads, 2) rclus_kernel(const SweepArgs<fl
         }
     };
 
-    // one pass over rows j .. j+NR-1 (same class)
-    auto pass = [&](auto nr_tag, int j) {
-        constexpr int NR = decltype(nr_tag)::value;
-        static_assert(MODE == MODE_DELTA || NR == 1, "the refined pass takes one row");
-        rb_wait<NRING - 2 - NR>();
-        // rows j-1 .. j+NR from the ring (ghost rows at the z faces); the
-        // refined pass reads them again after its first solve rather than
-        // holding them in registers through it
-        auto load_rows = [&](real(&x)[NR + 2][K]) {
-            auto ld_row = [&](int q, int r) {
-                const real *p = ring + (size_t)((r - jstart + 1) & (NRING - 1)) * kRcSeg;
+    // row r of the field from this thread's ring slot into v; ghost values
+    // at the z faces (r outside the field) and past the outer r face
+    auto ring_row = [&](int r, real(&v)[K]) {
+        if (r < 0 || r >= Nz) {
 #pragma unroll
-                for (int k = 0; k < K; k += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(p + k);
-                    x[q][k] = v.x, x[q][k + 1] = v.y, x[q][k + 2] = v.z, x[q][k + 3] = v.w;
-                }
-            };
-            if (j >= 1 && j + NR < Nz) {
+            for (int k = 0; k < K; ++k) v[k] = r < 0 ? bc2 : bc3;
+            return;
+        }
+        const real *p = ring + (size_t)((r - jstart + 1) & (NRING - 1)) * kRcSeg;
 #pragma unroll
-                for (int q = 0; q < NR + 2; ++q) ld_row(q, j - 1 + q);
-            } else {
+        for (int k = 0; k < K; k += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(p + k);
+            v[k] = q.x, v[k + 1] = q.y, v[k + 2] = q.z, v[k + 3] = q.w;
+        }
+        if (!EXACT && i0 + K > Nr)
 #pragma unroll
-                for (int q = 0; q < NR + 2; ++q) {
-                    const int r = j - 1 + q;
-                    if (r < 0 || r >= Nz) {
+            for (int k = 0; k < K; ++k)
+                if (i0 + k >= Nr) v[k] = bc1;
+    };
+    // theta of row jr at the chunk's outer neighbours (shuffles; across a
+    // warp edge from global memory; ghosts at the r faces)
+    auto row_nb = [&](int jr, const real(&xc)[K], real &nl, real &nrt) {
+        nl = __shfl_up_sync(FULL, xc[K - 1], 1);
+        nrt = __shfl_down_sync(FULL, xc[0], 1);
+        if (lane == 0) nl = (i0 > 0 && (EXACT || i0 - 1 < Nr)) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
+        if (lane == 31) nrt = (i0 + K < Nr) ? th[(size_t)jr * Nr + i0 + K] : bc1;
+    };
+    // right-hand side of row jr times the pivot, from rows jr-1, jr, jr+1
+    auto row_rhs = [&](int jr, const real(&xm)[K], const real(&xc)[K], const real(&xp)[K], real(&d)[K], real nl,
+                       real nrt) {
+        const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
+        const real zmA = Z.xm[zo], zpA = Z.xp[zo], zmB = Z.xm[zo1], zpB = Z.xp[zo1];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) x[q][k] = r < 0 ? bc2 : bc3;
-                    } else {
-                        ld_row(q, r);
-                    }
-                }
-            }
-            if (!EXACT && i0 + K > Nr)
-#pragma unroll
-                for (int q = 0; q < NR + 2; ++q)
-#pragma unroll
-                    for (int k = 0; k < K; ++k)
-                        if (i0 + k >= Nr && j - 1 + q >= 0 && j - 1 + q < Nz) x[q][k] = bc1;  // ghost past the outer r face
-        };
-        real x[NR + 2][K];
-        load_rows(x);
-        // right-hand sides times the pivot; nb[r]: row j+r's neighbours of the chunk ends
-        real d[2][K];
-        real nbl[NR], nbr[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int jr = min(j + r, Nz - 1);
-            const real *xr = x[r + 1];
-            real nl = __shfl_up_sync(FULL, xr[K - 1], 1);
-            real nrt = __shfl_down_sync(FULL, xr[0], 1);
-            if (lane == 0) nl = (i0 > 0 && (EXACT || i0 - 1 < Nr)) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
-            if (lane == 31) nrt = (i0 + K < Nr) ? th[(size_t)jr * Nr + i0 + K] : bc1;
-            nbl[r] = nl;
-            nbr[r] = nrt;
-            const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
-            const real zmA = Z.xm[zo], zpA = Z.xp[zo], zmB = Z.xm[zo1], zpB = Z.xp[zo1];
+        for (int k = 0; k < K; ++k) {
+            const real t0 = xc[k];
+            const real l = k > 0 ? xc[k - 1] : nl;
+            const real rr = k < K - 1 ? xc[k + 1] : nrt;
+            real v = fmad(fx[k], l - t0, qi[k]);
+            v = fmad(cx[k], rr - t0, v);
+            const bool bsel = (zsel >> k) & 1u;
+            const real zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
+            const real zz = fmad(zp, xp[k] - t0, zm * (xm[k] - t0));
+            d[k] = fmad(iv[k], zz, v);
+        }
+        if (zany) {
+            // a chunk with a third column class: per-cell z coefficients
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const real xc = xr[k];
-                const real l = k > 0 ? xr[k - 1] : nl;
-                const real rr = k < K - 1 ? xr[k + 1] : nrt;
-                real v = fmad(fx[k], l - xc, qi[k]);
-                v = fmad(cx[k], rr - xc, v);
-                const bool bsel = (zsel >> k) & 1u;
-                const real zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
-                const real zz = fmad(zp, x[r + 2][k] - xc, zm * (x[r][k] - xc));
-                d[r][k] = fmad(iv[k], zz, v);
-            }
-            if (zany) {
-                // a chunk with a third column class: per-cell z coefficients
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int i = i0 + k;
-                    if (i < Nr && colcls[i] != zc0 && colcls[i] != zc1) {
-                        const size_t zk = (size_t)colcls[i] * Nz + jr;
-                        const real xc = xr[k];
-                        const real l = k > 0 ? xr[k - 1] : nl;
-                        const real rr = k < K - 1 ? xr[k + 1] : nrt;
-                        real v = fmad(fx[k], l - xc, qi[k]);
-                        v = fmad(cx[k], rr - xc, v);
-                        const real zz = fmad(Z.xp[zk], x[r + 2][k] - xc, Z.xm[zk] * (x[r][k] - xc));
-                        d[r][k] = fmad(iv[k], zz, v);
-                    }
+                const int i = i0 + k;
+                if (i < Nr && colcls[i] != zc0 && colcls[i] != zc1) {
+                    const size_t zk = (size_t)colcls[i] * Nz + jr;
+                    const real t0 = xc[k];
+                    const real l = k > 0 ? xc[k - 1] : nl;
+                    const real rr = k < K - 1 ? xc[k + 1] : nrt;
+                    real v = fmad(fx[k], l - t0, qi[k]);
+                    v = fmad(cx[k], rr - t0, v);
+                    const real zz = fmad(Z.xp[zk], xp[k] - t0, Z.xm[zk] * (xm[k] - t0));
+                    d[k] = fmad(iv[k], zz, v);
                 }
             }
         }
-        solve(nr_tag, d);
-        if constexpr (MODE == MODE_REFINE) {
+    };
+    auto store_row = [&](int jr, const real(&v)[K]) {
+        real *orow = out + (size_t)jr * Nr;
+        if (EXACT || (vec && i0 + K <= Nr)) {
+#pragma unroll
+            for (int k = 0; k < K; k += 4)
+                *reinterpret_cast<float4 *>(orow + i0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (i0 + k < Nr) orow[i0 + k] = v[k];
+        }
+    };
+
+    if constexpr (MODE == MODE_DELTA) {
+        // one pass over rows j .. j+NR-1 (same class)
+        auto pass = [&](auto nr_tag, int j) {
+            constexpr int NR = decltype(nr_tag)::value;
+            rb_wait<NRING - 2 - NR>();
+            real x[NR + 2][K];
+#pragma unroll
+            for (int q = 0; q < NR + 2; ++q) ring_row(j - 1 + q, x[q]);
+            real d[2][K];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                real nl, nrt;
+                row_nb(j + r, x[r + 1], nl, nrt);
+                row_rhs(j + r, x[r], x[r + 1], x[r + 2], d[r], nl, nrt);
+            }
+            solve(nr_tag, d);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) d[r][k] = x[r + 1][k] + d[r][k];
+                store_row(j + r, d[r]);
+            }
+            // refill the slots of rows j-1 .. j+NR-2 with rows j+NRING-1 .. j+NRING+NR-2
+#pragma unroll
+            for (int r = 0; r < NR; ++r) fetch(j + NRING - 1 + r);
+        };
+        for (int t = 0; t < nrow;) {
+            const int j = jstart + t;
+            const int a = rowcls[j];
+            if (a != acls) load_class(a);  // the same rows, so the same decision, in every block
+            if (t + 1 < nrow && rowcls[j + 1] == a) {
+                pass(RbRows<2>(), j);
+                t += 2;
+            } else {
+                pass(RbRows<1>(), j);
+                t += 1;
+            }
+        }
+    } else {
+        // Refined rows, software-pipelined along the band: the correction
+        // solve of row j and the first solve of row j+1 (same class) share one
+        // two-row solve, so a row costs the delta0 exchange and one solve's
+        // two cluster barriers.  dl0 carries delta0 of row j into its step.
+        const LineTab2 &Z2 = A.Z2;
+        real dl0[K];
+        bool have = false;
+        for (int t = 0; t < nrow; ++t) {
+            const int j = jstart + t;
+            const int a = rowcls[j];
+            if (a != acls) load_class(a);  // no row of the previous class is in flight
+            real x[3][K];
+            real nl, nrt;
+            if (!have) {
+                // the first row of a run of one class: its first solve alone
+                rb_wait<0>();
+                ring_row(j - 1, x[0]);
+                ring_row(j, x[1]);
+                ring_row(j + 1, x[2]);
+                real d[2][K];
+                row_nb(j, x[1], nl, nrt);
+                row_rhs(j, x[0], x[1], x[2], d[0], nl, nrt);
+                solve(RbRows<1>(), d);
+#pragma unroll
+                for (int k = 0; k < K; ++k) dl0[k] = d[0][k];
+            }
             // delta0 of the neighbours of the chunk's end cells: within the
             // warp by shuffles, across warps and blocks through shared memory
-            real *dl0 = d[0];
             if (lane == 0) {
                 sLo[w] = dl0[0];
                 if (w == 0 && c > 0) rc_st(rc_map(&sER, c - 1), dl0[0]);
@@ -445,29 +496,29 @@ __global__ void __launch_bounds__(kRcThreads, 2) rclus_kernel(const SweepArgs<fl
             }
             real xl = __shfl_up_sync(FULL, dl0[K - 1], 1);
             real xr = __shfl_down_sync(FULL, dl0[0], 1);
+            const size_t zo = (size_t)zc0 * Nz + j, zo1 = (size_t)zc1 * Nz + j;
+            const float2 zmA = rc_ld2(Z2.am + zo), zpA = rc_ld2(Z2.ap + zo);
+            const float2 zmB = rc_ld2(Z2.am + zo1), zpB = rc_ld2(Z2.ap + zo1);
             rc_sync();
             if (lane == 0) xl = w > 0 ? sHi[w - 1] : (c > 0 ? sEL : real(0));
             if (lane == 31) xr = w < 7 ? sLo[w + 1] : (c < CL - 1 ? sER : real(0));
-            // residual of the increment system at delta0 from the FP64
-            // coefficients as FP32 pairs: q + sum c (t_nb - t) - b delta0
-            // + m delta0_{i-1} + p delta0_{i+1} (m = am, p = ap)
-            const LineTab2 &R2 = A.R2, &Z2 = A.Z2;
-            const int jr = min(j, Nz - 1);
-            const size_t ro = (size_t)acls * Nr;
-            const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
-            const float2 zmA = rc_ld2(Z2.am + zo), zpA = rc_ld2(Z2.ap + zo);
-            const float2 zmB = rc_ld2(Z2.am + zo1), zpB = rc_ld2(Z2.ap + zo1);
-            load_rows(x);
-            const real *xc = x[1];
-            real rho[K];
+            // residual of the increment system of row j at delta0, from the
+            // FP64 coefficients as FP32 pairs: q + sum c (t_nb - t) - b delta0
+            // + am delta0_{i-1} + ap delta0_{i+1} (the matrix's off-diagonals
+            // are the couplings am, ap themselves)
+            ring_row(j - 1, x[0]);
+            ring_row(j, x[1]);
+            ring_row(j + 1, x[2]);
+            row_nb(j, x[1], nl, nrt);
+            real d[2][K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int i = i0 + k;
-                rho[k] = real(0);
+                d[0][k] = real(0);
                 if (!EXACT && i >= Nr) continue;
-                const real t0 = xc[k];
-                const real tl = i == 0 ? t0 : (k > 0 ? xc[k - 1] : nbl[0]);
-                const real tr = i == Nr - 1 ? t0 : (k < K - 1 ? xc[k + 1] : nbr[0]);
+                const real t0 = x[1][k];
+                const real tl = i == 0 ? t0 : (k > 0 ? x[1][k - 1] : nl);
+                const real tr = i == Nr - 1 ? t0 : (k < K - 1 ? x[1][k + 1] : nrt);
                 const int sv = (k >> 1) * kRcThreads + tid, hi = k & 1;
                 const float4 Q4 = pairs[0 * (K / 2) * kRcThreads + sv], M4 = pairs[1 * (K / 2) * kRcThreads + sv];
                 const float4 P4 = pairs[2 * (K / 2) * kRcThreads + sv], B4 = pairs[3 * (K / 2) * kRcThreads + sv];
@@ -478,74 +529,51 @@ __global__ void __launch_bounds__(kRcThreads, 2) rclus_kernel(const SweepArgs<fl
                 Pair acc{q2.x, q2.y};
                 pair_add_cdiff(acc, am2, tl, t0);
                 pair_add_cdiff(acc, ap2, tr, t0);
-                if (i == 0) pair_add_cdiff(acc, rc_ld2(R2.dl + ro), bc0, t0);
-                if (i == Nr - 1) pair_add_cdiff(acc, rc_ld2(R2.dh + ro + i), bc1, t0);
+                if (i == 0) pair_add_cdiff(acc, rc_ld2(A.R2.dl + (size_t)acls * Nr), bc0, t0);
+                if (i == Nr - 1) pair_add_cdiff(acc, rc_ld2(A.R2.dh + (size_t)acls * Nr + i), bc1, t0);
                 const bool bsel = (zsel >> k) & 1u;
                 float2 zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
                 size_t zk = bsel ? zo1 : zo;
                 if (zany && colcls[i] != zc0 && colcls[i] != zc1) {
-                    zk = (size_t)colcls[i] * Nz + jr;
+                    zk = (size_t)colcls[i] * Nz + j;
                     zm = rc_ld2(Z2.am + zk);
                     zp = rc_ld2(Z2.ap + zk);
                 }
-                pair_add_cdiff(acc, zm, x[0][k], t0);  // row j-1 (ghost at the z face, where zm = 0)
+                pair_add_cdiff(acc, zm, x[0][k], t0);  // row j-1 (a ghost at the z face, where zm = 0)
                 pair_add_cdiff(acc, zp, x[2][k], t0);
-                if (jr == 0) pair_add_cdiff(acc, rc_ld2(Z2.dl + zk), bc2, t0);
-                if (jr == Nz - 1) pair_add_cdiff(acc, rc_ld2(Z2.dh + zk), bc3, t0);
+                if (j == 0) pair_add_cdiff(acc, rc_ld2(Z2.dl + zk), bc2, t0);
+                if (j == Nz - 1) pair_add_cdiff(acc, rc_ld2(Z2.dh + zk), bc3, t0);
                 const real xm = k > 0 ? dl0[k - 1] : xl;
                 const real xp = k < K - 1 ? dl0[k + 1] : xr;
                 pair_add_cx(acc, b2, -dl0[k]);
                 pair_add_cx(acc, am2, xm);
                 pair_add_cx(acc, ap2, xp);
-                rho[k] = __fadd_rn(acc.hi, acc.lo);
+                d[0][k] = __fadd_rn(acc.hi, acc.lo) * iv[k];  // the correction's right-hand side times the pivot
             }
-            // the correction: the same line systems with the residual as right-hand side
-            real e[2][K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) e[0][k] = rho[k] * iv[k];
-            solve(nr_tag, e);
-            // theta of row j once more from the ring (not held through the solve)
-            load_rows(x);
-#pragma unroll
-            for (int k = 0; k < K; ++k) d[0][k] = x[1][k] + (dl0[k] + e[0][k]);
-        } else {
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-#pragma unroll
-                for (int k = 0; k < K; ++k) d[r][k] = x[r + 1][k] + d[r][k];
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (j + r >= Nz) continue;
-            real *orow = out + (size_t)(j + r) * Nr;
-            if (EXACT || (vec && i0 + K <= Nr)) {
-#pragma unroll
-                for (int k = 0; k < K; k += 4)
-                    *reinterpret_cast<float4 *>(orow + i0 + k) = make_float4(d[r][k], d[r][k + 1], d[r][k + 2], d[r][k + 3]);
+            const bool next = t + 1 < nrow && rowcls[j + 1] == a;
+            if (next) {
+                // row j+1's first solve rides along: its rows j .. j+2
+                rb_wait<0>();
+                ring_row(j + 2, x[0]);  // rows j, j+1 are x[1], x[2]
+                real nl1, nr1;
+                row_nb(j + 1, x[2], nl1, nr1);
+                row_rhs(j + 1, x[1], x[2], x[0], d[1], nl1, nr1);
+                solve(RbRows<2>(), d);
             } else {
-#pragma unroll
-                for (int k = 0; k < K; ++k)
-                    if (i0 + k < Nr) orow[i0 + k] = d[r][k];
+                solve(RbRows<1>(), d);
             }
-        }
-        // refill the slots of rows j-1 .. j+NR-2 with rows j+NRING-1 .. j+NRING+NR-2
+            // row j: theta + (delta0 + e)
+            ring_row(j, x[1]);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) fetch(j + NRING - 1 + r);
-    };
-
-    for (int t = 0; t < nrow;) {
-        const int j = jstart + t;
-        const int a = rowcls[j];
-        if (a != acls) load_class(a);  // the same rows, so the same decision, in every block
-        if constexpr (MODE == MODE_DELTA) {
-            if (t + 1 < nrow && rowcls[j + 1] == a) {
-                pass(RbRows<2>(), j);
-                t += 2;
-                continue;
+            for (int k = 0; k < K; ++k) x[1][k] = x[1][k] + (dl0[k] + d[0][k]);
+            store_row(j, x[1]);
+            if (next) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) dl0[k] = d[1][k];
             }
+            have = next;
+            fetch(j + NRING - 1);  // row j+3 into the slot of row j-1
         }
-        pass(RbRows<1>(), j);
-        t += 1;
     }
     rb_wait<0>();
     // no block leaves while another may still address its shared memory
