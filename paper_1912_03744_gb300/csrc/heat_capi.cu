@@ -145,10 +145,10 @@ int upload_zpart(heat_ctx *ctx)
         HEAT_CHECK(cudaMemcpyAsync(z.ucls, u.data(), u.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     }
     {
-        // (FP32 increment path only: the FP64 passes spill with the tile
-        // bookkeeping and ran slower tiled; the refined path has no lean passes)
+        // (FP32 paths only: the FP64 passes spill with the tile bookkeeping
+        // and ran slower tiled)
         std::vector<int> t;
-        if (ctx->precision == HEAT_FP32) t = z_tiles(ctx->g.colcls, ctx->g.Nr, 4);
+        if (ctx->precision != HEAT_FP64) t = z_tiles(ctx->g.colcls, ctx->g.Nr, 4);
         if (z.tiles) cudaFree(z.tiles), z.tiles = nullptr;
         z.n_tiles = (int)t.size() / 4;
         if (z.n_tiles) {

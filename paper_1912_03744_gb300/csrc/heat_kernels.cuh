@@ -1581,7 +1581,10 @@ static cudaError_t plan_rsweep(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 // One z pass: chunk summaries, carries, chunk solves, for n instances
 // (instance m in the last grid dimension; blocks past an instance's columns
 // or chunks return at once).
-template <typename real, int MODE>
+// OUT selects the solve pass's output (zsolve2_kernel) and CSUM the summary
+// pass that reads its right-hand side from the output buffer (zsumc_kernel):
+// the two z solves of the refined path.
+template <typename real, int MODE, int OUT = ZOUT_FIELD, bool CSUM = false>
 static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::vector<Launch> &out)
 {
     constexpr int V = 16 / (int)sizeof(real);
@@ -1617,6 +1620,10 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     a.fn = !lean      ? (const void *)zsum_kernel<real, V, MODE>
            : nitem > 0 ? (const void *)zsum2_kernel<real, V, LM, true>
                        : (const void *)zsum2_kernel<real, V, LM, false>;
+    if constexpr (CSUM) {
+        static_assert(sizeof(real) == 4 && lean, "the correction summary is FP32, lean");
+        a.fn = nitem > 0 ? (const void *)zsumc_kernel<V, true> : (const void *)zsumc_kernel<V, false>;
+    }
     a.grid = lean ? lean_grid(SWPB) : dim3((groups + SWPB - 1) / SWPB, maxNch, n);
     a.block = dim3(32 * SWPB, 1, 1);
     a.smem = (size_t)SWPB * maxRc * 8 * sizeof(real);
@@ -1643,8 +1650,8 @@ static cudaError_t plan_zpass(const SweepArgs<real> *h, int n, Tuning &tu, std::
     // summary pass: 1 for a single tiled instance), staged (P, cp) rows only
     const int cw = lean ? SWPB : wpb;
     c.fn = !lean      ? (const void *)zsolve_kernel<real, V, MODE>
-           : nitem > 0 ? (const void *)zsolve2_kernel<real, V, LM, true>
-                       : (const void *)zsolve2_kernel<real, V, LM, false>;
+           : nitem > 0 ? (const void *)zsolve2_kernel<real, V, LM, true, OUT>
+                       : (const void *)zsolve2_kernel<real, V, LM, false, OUT>;
     c.grid = lean ? lean_grid(cw) : dim3((groups + cw - 1) / cw, maxNch, n);
     c.block = dim3(32 * cw, 1, 1);
     c.smem = lean ? (size_t)cw * ZNC * maxRc * 2 * sizeof(real) : (size_t)wpb * maxRc * (COLS + 8) * sizeof(real);
@@ -1720,8 +1727,25 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     if (e != cudaSuccess) return e;
     plan.dir[0].push_back(r);
     if constexpr (MODE == MODE_REFINE) {
-        if ((e = plan_zpass<real, MODE_REFINE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
-        if ((e = plan_zpass<real, MODE_CORR>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+        if (n == 1) {
+            // lean passes: delta0 into the rho buffer; the residual at delta0
+            // (zres_kernel) into the output buffer; the correction's summary
+            // from it and the solve that stores theta + (delta0 + e)
+            if ((e = plan_zpass<real, MODE_DELTA, ZOUT_DELTA0>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+            Launch rz;
+            constexpr int V = 4;
+            const int warps = (h[0].Nr + 32 * V - 1) / (32 * V);
+            rz.fn = (const void *)zres_kernel<V>;
+            rz.grid = dim3((warps + 3) / 4, (h[0].Nz + kZResRows - 1) / kZResRows, 1);
+            rz.block = dim3(128, 1, 1);
+            rz.smem = 0;
+            rz.flip = true;
+            plan.dir[1].push_back(rz);
+            if ((e = plan_zpass<real, MODE_DELTA, ZOUT_CORR, true>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+        } else {
+            if ((e = plan_zpass<real, MODE_REFINE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+            if ((e = plan_zpass<real, MODE_CORR>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
+        }
     } else {
         if ((e = plan_zpass<real, MODE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
     }

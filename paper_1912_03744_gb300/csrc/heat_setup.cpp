@@ -284,10 +284,12 @@ void build_zpartition(heat_ctx *ctx)
     ctx->zpk.assign((size_t)nb * Nz * 8, 0.0);
     ctx->zch.assign((size_t)nb * nch * 4, 0.0);
     const bool lit = ctx->precision == HEAT_FP64;
-    // the refined path's summary pass weights its rows by wB; the literal and
-    // increment paths take B from the zero-carry recurrence itself and need
-    // the prefix products P_j = prod f from the chunk's first row instead
-    const bool prefix = ctx->precision != HEAT_FP32_REFINED;
+    // the refined path of a batch member (the non-lean passes) weights its
+    // summary rows by wB; the literal and increment paths, and the lean
+    // passes of a single refined context, take B from the zero-carry
+    // recurrence itself and need the prefix products P_j = prod f from the
+    // chunk's first row instead
+    const bool prefix = ctx->precision != HEAT_FP32_REFINED || !ctx->batch_member;
     std::vector<double> wB(Rc), wG(Rc), Pp(Rc);
     for (int b = 0; b < nb; ++b) {
         const size_t o = (size_t)b * Nz;

@@ -552,11 +552,16 @@ __global__ void __launch_bounds__(128, 4) zsum2_kernel(const SweepArgs<real> *__
 //   x_j  = d'_j + cp_j x_{j+1},
 // and the new field is theta + x (increment form) or x (literal form).  Rows
 // of d0 and theta are fetched ZQ at a time, double-buffered.
-template <typename real, int V, int MODE, bool ITEMS>
+// OUT (increment form, the refined z-sweep): ZOUT_DELTA0 stores x itself in
+// the rho buffer (delta0 of the first solve); ZOUT_CORR stores
+// theta + (delta0 + x) with delta0 read from the rho buffer (x the correction).
+enum { ZOUT_FIELD = 0, ZOUT_DELTA0 = 1, ZOUT_CORR = 2 };
+template <typename real, int V, int MODE, bool ITEMS, int OUT = ZOUT_FIELD>
 __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const SweepArgs<real> *__restrict__ args, int flip)
 {
     pdl_launch_dependents();
-    constexpr bool LIT = MODE == MODE_LIT;
+    constexpr bool LIT = MODE == MODE_LIT || OUT == ZOUT_DELTA0;  // no theta to add
+    static_assert(OUT == ZOUT_FIELD || MODE == MODE_DELTA, "refined outputs are increment forms");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int grp = blockIdx.x * (blockDim.x >> 5) + w;
     int mi, c, wb, lo, hi;
@@ -564,6 +569,8 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
     const SweepArgs<real> &A = args[mi];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;  // holds d0 on entry
+    real *__restrict__ dst = OUT == ZOUT_DELTA0 ? A.rho : out;
+    const real *__restrict__ dl0 = A.rho;  // ZOUT_CORR: delta0
     const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
     const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
     const int ib = wb + lane * V;
@@ -634,17 +641,18 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
             for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : real(0);
         }
     };
-    auto fetch = [&](int x0, real (&dz)[ZQ][V], real (&bs)[ZQ][V]) {
+    auto fetch = [&](int x0, real (&dz)[ZQ][V], real (&bs)[ZQ][V], real (&ds)[ZQ][V]) {
 #pragma unroll
         for (int p = 0; p < ZQ; ++p) {
             const int j = x0 - p;
             if (j >= j0) {
                 ldrow(out, j, dz[p]);
                 if constexpr (!LIT) ldrow(th, j, bs[p]);
+                if constexpr (OUT == ZOUT_CORR) ldrow(dl0, j, ds[p]);
             }
         }
     };
-    auto proc = [&](int x0, const real (&dz)[ZQ][V], const real (&bs)[ZQ][V]) {
+    auto proc = [&](int x0, const real (&dz)[ZQ][V], const real (&bs)[ZQ][V], const real (&ds)[ZQ][V]) {
 #pragma unroll
         for (int p = 0; p < ZQ; ++p) {
             const int j = x0 - p;
@@ -666,13 +674,14 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
                     x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
-                    o[q] = LIT ? x[q] : bs[p][q] + x[q];
+                    o[q] = LIT ? x[q] : OUT == ZOUT_CORR ? bs[p][q] + (ds[p][q] + x[q]) : bs[p][q] + x[q];
                 }
-                put(out + (size_t)j * Nr + ib, o);
+                put(dst + (size_t)j * Nr + ib, o);
             }
         }
     };
     real da[ZQ][V], ba[ZQ][V], db[ZQ][V], bb[ZQ][V];
+    real sa[ZQ][V], sb[ZQ][V];  // ZOUT_CORR: delta0 rows
     if (few && (j1 - j0) % (2 * ZQ) == 0) {
         // a full chunk: no row needs a bounds check; running row pointers.
         // TM = 1: one class (one staged (P, cp) pair per row), else per
@@ -683,8 +692,8 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
         auto lean = [&](auto tm_tag, auto vec_tag) {
             constexpr int TM = decltype(tm_tag)::value;
             constexpr bool VEC = decltype(vec_tag)::value;
-            const real *dp = out + o1, *tp = th + o1;
-            real *op = out + o1;
+            const real *dp = out + o1, *tp = th + o1, *lp = dl0 + o1;
+            real *op = dst + o1;
             int ro = 2 * (j1 - 1 - j0);
             auto ld = [&](const real *p, real(&v)[V]) {
                 if constexpr (VEC) {
@@ -699,16 +708,18 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
                     for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? __ldg(p + q) : real(0);
                 }
             };
-            auto fetchf = [&](real(&dz)[ZQ][V], real(&bs)[ZQ][V]) {
+            auto fetchf = [&](real(&dz)[ZQ][V], real(&bs)[ZQ][V], real(&ds)[ZQ][V]) {
 #pragma unroll
                 for (int p = 0; p < ZQ; ++p) {
                     ld(dp - p * S, dz[p]);
                     if constexpr (!LIT) ld(tp - p * S, bs[p]);
+                    if constexpr (OUT == ZOUT_CORR) ld(lp - p * S, ds[p]);
                 }
                 dp -= ZQ * S;
                 tp -= ZQ * S;
+                lp -= ZQ * S;
             };
-            auto procf = [&](const real(&dz)[ZQ][V], const real(&bs)[ZQ][V]) {
+            auto procf = [&](const real(&dz)[ZQ][V], const real(&bs)[ZQ][V], const real(&ds)[ZQ][V]) {
 #pragma unroll
                 for (int p = 0; p < ZQ; ++p) {
                     real Pj[V], cpj[V];
@@ -725,19 +736,19 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
 #pragma unroll
                     for (int q = 0; q < V; ++q) {
                         x[q] = fmad(cpj[q], x[q], fmad(Pj[q], D[q], dz[p][q]));
-                        o[q] = LIT ? x[q] : bs[p][q] + x[q];
+                        o[q] = LIT ? x[q] : OUT == ZOUT_CORR ? bs[p][q] + (ds[p][q] + x[q]) : bs[p][q] + x[q];
                     }
                     put(op, o);
                     op -= S;
                 }
             };
-            fetchf(da, ba);
+            fetchf(da, ba, sa);
 #pragma unroll 1
             for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
-                fetchf(db, bb);
-                procf(da, ba);
-                if (x0 - 2 * ZQ >= j0) fetchf(da, ba);
-                procf(db, bb);
+                fetchf(db, bb, sb);
+                procf(da, ba, sa);
+                if (x0 - 2 * ZQ >= j0) fetchf(da, ba, sa);
+                procf(db, bb, sb);
             }
         };
         using One = std::integral_constant<int, 1>;
@@ -757,15 +768,232 @@ __global__ void __launch_bounds__(128, ITEMS ? 4 : 1) zsolve2_kernel(const Sweep
         }
         return;
     }
-    fetch(j1 - 1, da, ba);
+    fetch(j1 - 1, da, ba, sa);
 #pragma unroll 1
     for (int x0 = j1 - 1; x0 >= j0; x0 -= 2 * ZQ) {
         const bool h1 = x0 - ZQ >= j0;
-        if (h1) fetch(x0 - ZQ, db, bb);
-        proc(x0, da, ba);
+        if (h1) fetch(x0 - ZQ, db, bb, sb);
+        proc(x0, da, ba, sa);
         if (h1) {
-            if (x0 - 2 * ZQ >= j0) fetch(x0 - 2 * ZQ, da, ba);
-            proc(x0 - ZQ, db, bb);
+            if (x0 - 2 * ZQ >= j0) fetch(x0 - 2 * ZQ, da, ba, sa);
+            proc(x0 - ZQ, db, bb, sb);
+        }
+    }
+}
+
+// Summary pass of the refined z-sweep's correction: zsum2 with the residual
+// rho_j (stored in the output buffer by zres_kernel) as the right-hand side
+// of row j; the forward results d0 replace it in place (each lane reads its
+// stored columns before writing them).
+template <int V, bool ITEMS>
+__global__ void __launch_bounds__(128, 4) zsumc_kernel(const SweepArgs<float> *__restrict__ args, int flip)
+{
+    using real = float;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int grp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int mi, c, wb, lo, hi;
+    if (!zl_work<real, V, ITEMS>(args, grp, mi, c, wb, lo, hi)) return;  // no work (warp-uniform)
+    const SweepArgs<real> &A = args[mi];
+    const int Nr = A.Nr, Nz = A.Nz, Rc = A.Rc;
+    const int j0 = c * Rc, j1 = min(Nz, j0 + Rc);
+    real *__restrict__ io = flip ? A.f0 : A.f1;
+    ZWalk<real, V, MODE_DELTA> W;
+    W.init(A, flip ? A.f1 : A.f0, wb + lane * V, lane, j0, j1, lo, hi);
+    real dl[V], sg[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) dl[q] = sg[q] = real(0);
+    extern __shared__ __align__(16) unsigned char zc_smem[];
+    const bool one = W.warp_uniform();
+    if (one) {
+        const int Rs = ITEMS ? args[0].zrc_max : Rc;
+        W.stage(reinterpret_cast<real *>(zc_smem) + (size_t)(threadIdx.x >> 5) * Rs * 8);
+    }
+    pdl_wait();
+    auto run = [&](auto e_tag) {
+        constexpr int E = decltype(e_tag)::value;
+        real ra[ZQ][V], rb[ZQ][V];
+        auto fetch = [&](int x, real(&r)[ZQ][V]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p)
+                if (x + p < j1) W.row(io, x + p, r[p]);
+        };
+        auto proc = [&](int x, const real(&r)[ZQ][V]) {
+#pragma unroll
+            for (int p = 0; p < ZQ; ++p) {
+                const int j = x + p;
+                if (j < j1) {
+                    real e[E][8];
+                    W.template tab<E>(j, e);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        dl[q] = fmad(r[p][q], e[E == 1 ? 0 : q][0], e[E == 1 ? 0 : q][1] * dl[q]);
+                        sg[q] = fmad(r[p][q], e[E == 1 ? 0 : q][7], sg[q]);
+                    }
+                    W.put(io + (size_t)j * Nr + W.ib, dl);
+                }
+            }
+        };
+        fetch(j0, ra);
+#pragma unroll 1
+        for (int x = j0; x < j1; x += 2 * ZQ) {
+            const bool h1 = x + ZQ < j1;
+            if (h1) fetch(x + ZQ, rb);
+            proc(x, ra);
+            if (h1) {
+                if (x + 2 * ZQ < j1) fetch(x + 2 * ZQ, ra);
+                proc(x + ZQ, rb);
+            }
+        }
+    };
+    if (one)
+        run(std::integral_constant<int, 1>());
+    else
+        run(std::integral_constant<int, V>());
+    real *__restrict__ zs = A.zs;
+    W.put(zs + ((size_t)c * 2) * Nr + W.ib, dl);
+    W.put(zs + ((size_t)c * 2 + 1) * Nr + W.ib, sg);
+}
+
+// Residual of the refined z-sweep's line systems at delta0 (the first
+// solve's increment, in the rho buffer), for every cell, into the output
+// buffer: rho = q + sum over the four neighbours of c (theta_nb - theta)
+// - b delta0 + am delta0_{j-1} + ap delta0_{j+1}, the z-couplings (am, ap,
+// b, q) of the cell's column class and the r-couplings of its row class
+// from the FP64 tables as FP32 pairs, with exact differences and FMA
+// products (Pair in heat_kernels.cuh).  Dirichlet faces enter as couplings
+// (dl, dh) to the ghost value theta_bc.  A warp owns 32 V adjacent columns
+// and walks kZResRows rows, the next rows' loads in flight.
+constexpr int kZResRows = 32;
+template <int V>
+__global__ void __launch_bounds__(128) zres_kernel(const SweepArgs<float> *__restrict__ args, int flip)
+{
+    using real = float;
+    pdl_launch_dependents();
+    const SweepArgs<real> &A = args[0];
+    const real *__restrict__ th = flip ? A.f1 : A.f0;
+    real *__restrict__ out = flip ? A.f0 : A.f1;
+    const real *__restrict__ dz = A.rho;
+    const int Nr = A.Nr, Nz = A.Nz;
+    const int lane = threadIdx.x & 31;
+    const int wcol = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * V;
+    if (wcol >= Nr) return;  // warp-uniform
+    const int ib = wcol + lane * V;
+    const int j0 = blockIdx.y * kZResRows, j1 = min(Nz, j0 + kZResRows);
+    const bool any = ib < Nr, vec = (Nr % V) == 0;
+    const real bz_lo = (real)A.bc.th[2], bz_hi = (real)A.bc.th[3];
+    const real br_lo = (real)A.bc.th[0], br_hi = (real)A.bc.th[1];
+    const LineTab2 &R2 = A.R2, &Z2 = A.Z2;
+    int b[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) b[q] = ib + q < Nr ? A.colcls[ib + q] : (any ? A.colcls[ib] : 0);
+    bool uni = true;
+#pragma unroll
+    for (int q = 1; q < V; ++q) uni = uni && b[q] == b[0];
+    auto trow = [&](int j, real(&v)[V]) {
+        if (j < 0 || j >= Nz) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = j < 0 ? bz_lo : bz_hi;
+            return;
+        }
+        const real *p = th + (size_t)j * Nr + ib;
+        if (vec && any) {
+            ZVec<real, V>::ld(p, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : br_hi;
+        }
+    };
+    auto drow = [&](int j, real(&v)[V]) {
+        if (j < 0 || j >= Nz) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = real(0);
+            return;
+        }
+        const real *p = dz + (size_t)j * Nr + ib;
+        if (vec && any) {
+            ZVec<real, V>::ld(p, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = ib + q < Nr ? p[q] : real(0);
+        }
+    };
+    pdl_wait();
+    // rows j-1, j (tm, t; dm, dc) and the prefetched row j+1 (tp, dp)
+    real tm[V], t[V], tp[V], dm[V], dc[V], dp[V];
+    trow(j0 - 1, tm);
+    trow(j0, t);
+    drow(j0 - 1, dm);
+    drow(j0, dc);
+    trow(j0 + 1, tp);
+    drow(j0 + 1, dp);
+    int acur = -1;
+    float2 A0[V], A1[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) A0[q] = A1[q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) {
+        // the row after next in flight while this one is computed
+        real tn[V], dn[V];
+        trow(j + 2, tn);
+        drow(j + 2, dn);
+        real tl = __shfl_up_sync(HEAT_FULL_MASK, t[V - 1], 1);
+        real tr = __shfl_down_sync(HEAT_FULL_MASK, t[0], 1);
+        if (lane == 0) tl = ib > 0 && ib - 1 < Nr ? th[(size_t)j * Nr + ib - 1] : br_lo;
+        if (lane == 31) tr = ib + V < Nr ? th[(size_t)j * Nr + ib + V] : br_hi;
+        const int a = A.rowcls[j];
+        if (a != acur) {
+            acur = a;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int i = ib + q;
+                const size_t ro = (size_t)a * Nr + i;
+                A0[q] = i < Nr ? (i == 0 ? R2.dl[ro] : R2.am[ro]) : make_float2(0.f, 0.f);
+                A1[q] = i < Nr ? (i == Nr - 1 ? R2.dh[ro] : R2.ap[ro]) : make_float2(0.f, 0.f);
+            }
+        }
+        real rr[V];
+        float2 cq, cm, cp, cb, fm, fp;  // z pairs of the class: q, am, ap, b; face couplings of the theta terms
+        auto zload = [&](int cls) {
+            const size_t zj = (size_t)cls * Nz + j;
+            cq = __ldg(Z2.q + zj);
+            cm = __ldg(Z2.am + zj);
+            cp = __ldg(Z2.ap + zj);
+            cb = __ldg(Z2.b + zj);
+            fm = j == 0 ? __ldg(Z2.dl + zj) : cm;
+            fp = j == Nz - 1 ? __ldg(Z2.dh + zj) : cp;
+        };
+        if (uni) zload(b[0]);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            if (!uni) zload(b[q]);
+            const real x = t[q];
+            const real l = q > 0 ? t[q - 1] : tl;
+            const real r = q < V - 1 ? t[q + 1] : tr;
+            Pair acc{cq.x, cq.y};
+            pair_add_cdiff(acc, fm, tm[q], x);
+            pair_add_cdiff(acc, fp, tp[q], x);
+            pair_add_cdiff(acc, A0[q], l, x);
+            pair_add_cdiff(acc, A1[q], r, x);
+            pair_add_cx(acc, cb, -dc[q]);
+            pair_add_cx(acc, cm, dm[q]);
+            pair_add_cx(acc, cp, dp[q]);
+            rr[q] = __fadd_rn(acc.hi, acc.lo);
+        }
+        if (any) {
+            real *o = out + (size_t)j * Nr + ib;
+            if (vec) {
+                ZVec<real, V>::st(o, rr);
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    if (ib + q < Nr) o[q] = rr[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            tm[q] = t[q], t[q] = tp[q], tp[q] = tn[q];
+            dm[q] = dc[q], dc[q] = dp[q], dp[q] = dn[q];
         }
     }
 }
