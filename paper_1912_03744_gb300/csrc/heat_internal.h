@@ -155,6 +155,7 @@ struct Launch {
     size_t smem = 0;
     bool flip = false;
     int cluster = 1;  // blocks per thread-block cluster along x (1: no cluster)
+    bool pdl = true;  // launched with programmatic stream serialization
 };
 
 // Launch schedule of both half-steps for one set of instances (one problem,

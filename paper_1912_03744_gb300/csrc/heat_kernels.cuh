@@ -1551,6 +1551,11 @@ static cudaError_t plan_rclus(SweepArgs<float> *h, int n, Tuning &tu, Launch &L)
     L.smem = smem;
     L.flip = true;
     L.cluster = CL;
+    // no early launch: blocks of a cluster are placed together, and placed
+    // while the previous kernel's blocks still hold the SMs they land
+    // unevenly, so that part of the band-sized grid waited for a second wave
+    // (refined steps back to back: 773 us against 602 us one at a time)
+    L.pdl = false;
     return cudaSuccess;
 }
 

@@ -124,7 +124,7 @@ cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int fli
         cfg.stream = s;
         cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        attr[0].val.programmaticStreamSerializationAllowed = L.pdl ? 1 : 0;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         if (L.cluster > 1) {
