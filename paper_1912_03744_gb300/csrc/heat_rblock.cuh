@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         }
 
     const bool zany = __any_sync(FULL, zmany);
+    const bool zone = __all_sync(FULL, zsel == 0u && !zmany);  // one column class in every chunk of the warp
     pdl_wait();
     // prologue: rows jstart-1 .. jstart+NRING-2
     for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
@@ -259,20 +260,36 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             real nrt = __shfl_down_sync(FULL, xr[0], 1, W);
             if (ls == 0) nl = (i0 > 0 && (EXACT || i0 - 1 < Nr)) ? th[(size_t)jr * Nr + i0 - 1] : bc0;
             if (ls == W - 1) nrt = (i0 + K < Nr) ? th[(size_t)jr * Nr + i0 + K] : bc1;
-            const size_t zo = (size_t)zc0 * Nz + jr, zo1 = (size_t)zc1 * Nz + jr;
-            const real zmA = Z.xm[zo], zpA = Z.xp[zo], zmB = Z.xm[zo1], zpB = Z.xp[zo1];
+            const size_t zo = (size_t)zc0 * Nz + jr;
+            const real zmA = Z.xm[zo], zpA = Z.xp[zo];
+            if (zone) {
+                // every chunk of the warp has one column class
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                // the right-hand side times the pivot inv
-                const real xc = xr[k];
-                const real l = k > 0 ? xr[k - 1] : nl;
-                const real rr = k < K - 1 ? xr[k + 1] : nrt;
-                real v = fmad(fx[k], l - xc, qi[k]);
-                v = fmad(cx[k], rr - xc, v);
-                const bool bsel = (zsel >> k) & 1u;
-                const real zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
-                const real zz = fmad(zp, x[r + 2][k] - xc, zm * (x[r][k] - xc));
-                d[r][k] = fmad(iv[k], zz, v);
+                for (int k = 0; k < K; ++k) {
+                    const real xc = xr[k];
+                    const real l = k > 0 ? xr[k - 1] : nl;
+                    const real rr = k < K - 1 ? xr[k + 1] : nrt;
+                    real v = fmad(fx[k], l - xc, qi[k]);
+                    v = fmad(cx[k], rr - xc, v);
+                    const real zz = fmad(zpA, x[r + 2][k] - xc, zmA * (x[r][k] - xc));
+                    d[r][k] = fmad(iv[k], zz, v);
+                }
+            } else {
+                const size_t zo1 = (size_t)zc1 * Nz + jr;
+                const real zmB = Z.xm[zo1], zpB = Z.xp[zo1];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    // the right-hand side times the pivot inv
+                    const real xc = xr[k];
+                    const real l = k > 0 ? xr[k - 1] : nl;
+                    const real rr = k < K - 1 ? xr[k + 1] : nrt;
+                    real v = fmad(fx[k], l - xc, qi[k]);
+                    v = fmad(cx[k], rr - xc, v);
+                    const bool bsel = (zsel >> k) & 1u;
+                    const real zm = bsel ? zmB : zmA, zp = bsel ? zpB : zpA;
+                    const real zz = fmad(zp, x[r + 2][k] - xc, zm * (x[r][k] - xc));
+                    d[r][k] = fmad(iv[k], zz, v);
+                }
             }
             if (zany) {
                 // the chunk crosses a column-class boundary: per-cell z coefficients
