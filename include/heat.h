@@ -207,8 +207,12 @@ int heat_sync(heat_ctx *ctx);
 /* Failure-detection test hook: with on = 1, the walked r-sweep (heat_set_rsweep
  * kind 3, the one that stages rows by bulk copies on mbarriers) first waits,
  * with a 2 ms limit, on a barrier nothing completes, records the time-out and
- * skips the sweep; heat_sync then returns HEAT_ERR_TIMEOUT.  on = 0 restores
- * normal operation.  No GPU fault is involved.  Synchronizes. */
+ * skips the sweep; the persistent step kernel of a small FP64 instance
+ * (lines up to 256 cells each way, heat_step with the default r-sweep rule)
+ * waits at its first grid barrier for one block more than it has, gives up
+ * after 1 s, records the time-out and ends.  heat_sync then returns
+ * HEAT_ERR_TIMEOUT.  on = 0 restores normal operation.  No GPU fault is
+ * involved.  Synchronizes. */
 int heat_test_stall(heat_ctx *ctx, int on);
 
 void heat_destroy(heat_ctx *ctx);

@@ -21,6 +21,7 @@ bool build_rline(const heat_ctx *, int, size_t, int &, int &, std::vector<double
                  std::vector<double> &, std::vector<double> &, std::vector<int> &);
 cudaError_t launch_fill(heat_ctx *, int, double);
 cudaError_t launch_steps(heat_ctx *, int);
+cudaError_t small_setup(heat_ctx *);
 cudaError_t launch_sweep(heat_ctx *, int);
 cudaError_t ctx_plan(heat_ctx *);
 cudaError_t launch_energy(heat_ctx *);
@@ -268,7 +269,7 @@ void free_ctx(heat_ctx *ctx)
                     ctx->d_part,   ctx->d_res,      ctx->zp.pk64,    ctx->zp.ch64,  ctx->zp.pk32,
                     ctx->zp.ch32,  ctx->d_zsum,     ctx->d_zsum64,   ctx->d_rho,    ctx->zp.ucls,
                     ctx->d_args,   ctx->d_rl,       ctx->d_rlz,      ctx->zp.tiles, ctx->d_rwtab, ctx->d_rwcc,
-                    ctx->d_status};
+                    ctx->d_status, ctx->d_small_bar};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -400,6 +401,7 @@ int create_ctx(const heat_geometry *geom, const heat_materials *mat, const heat_
     HEAT_TRY(launch_fill(ctx, 0, mat->T_init - ctx->T_ref));
     HEAT_TRY(launch_fill(ctx, 1, mat->T_init - ctx->T_ref));
     HEAT_TRY(ctx_plan(ctx));
+    HEAT_TRY(small_setup(ctx));
     HEAT_TRY(cudaStreamSynchronize(ctx->stream));
 #undef HEAT_TRY
     *out = ctx;

@@ -310,4 +310,9 @@ struct heat_ctx {
     int rw_stall = 0;
     int *d_status = nullptr;            // bit 0: a kernel's bounded wait gave up
     int rsweep_req = 0;                 // requested r-sweep kernel (heat_set_rsweep; 0 = default rule)
+    // persistent whole-step kernel of a small FP64 instance (heat_small.cu;
+    // small_fn null when the instance does not qualify)
+    const void *small_fn = nullptr;
+    int small_blocks = 0, small_wpb = 1;
+    unsigned *d_small_bar = nullptr;    // grid barrier: the launch's arrival count (and a spare word)
 };

@@ -181,8 +181,11 @@ cudaError_t launch_sweep(heat_ctx *ctx, int dir)
     return run_plan(ctx->plan, dir, ctx->d_args, ctx->cur, ctx->stream);
 }
 
+cudaError_t launch_small_steps(heat_ctx *ctx, int n);
+
 cudaError_t launch_steps(heat_ctx *ctx, int n)
 {
+    if (ctx->small_fn && ctx->rsweep_req == 0) return launch_small_steps(ctx, n);
     for (int s = 0; s < n; ++s) {
         cudaError_t e = run_plan(ctx->plan, 0, ctx->d_args, ctx->cur, ctx->stream);
         if (e != cudaSuccess) return e;
@@ -192,7 +195,11 @@ cudaError_t launch_steps(heat_ctx *ctx, int n)
     return cudaSuccess;
 }
 
-int launches_per_step(const heat_ctx *ctx) { return (int)(ctx->plan.dir[0].size() + ctx->plan.dir[1].size()); }
+int launches_per_step(const heat_ctx *ctx)
+{
+    if (ctx->small_fn && ctx->rsweep_req == 0) return 1;  // (one launch runs all n steps)
+    return (int)(ctx->plan.dir[0].size() + ctx->plan.dir[1].size());
+}
 
 int energy_blocks(const heat_ctx *ctx)
 {

@@ -162,3 +162,39 @@ def test_bounded_wait_reports_a_timeout_and_the_context_recovers():
     assert L.heat_sync(s._h) == HEAT_OK
     assert float(np.max(np.abs(s.field() - o.field())) / np.max(np.abs(o.field()))) <= 1e-5
     s.close()
+
+
+@pytest.mark.gpu
+def test_grid_barrier_time_out_is_reported_and_the_context_recovers():
+    """The persistent step kernel of a small FP64 instance separates its half
+    steps by a grid barrier with a 1 s limit.  The test hook makes the first
+    barrier wait for one block more than the launch has: heat_sync must
+    return HEAT_ERR_TIMEOUT, and with the hook off the next steps must match
+    the oracle again."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import Oracle
+    from paper_1912_03744_gb300 import HeatSolver
+    from paper_1912_03744_gb300 import heat as hb
+    p = H.config1()
+    o = Oracle(p)
+    tau = 20.0 * o.tau_exp()
+    s = HeatSolver(p, tau, precision="fp64")
+    assert s.launches_per_step() == 1  # the persistent kernel
+    L = hb.load()
+    assert L.heat_test_stall(s._h, 1) == HEAT_OK
+    s.step(3)
+    assert L.heat_sync(s._h) == -4  # HEAT_ERR_TIMEOUT
+    assert L.heat_sync(s._h) == HEAT_OK
+    assert L.heat_test_stall(s._h, 0) == HEAT_OK
+    T0 = H.random_field(p, seed=6, amp=10.0)
+    s.set_field(T0)
+    o.set_field(T0)
+    s.step(4)
+    o.step(tau, 4)
+    assert L.heat_sync(s._h) == HEAT_OK
+    assert float(np.max(np.abs(s.field() - o.field())) / np.max(np.abs(o.field()))) <= 1e-12
+    s.close()
