@@ -186,9 +186,117 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
             }
 }
 
+// The network's pointwise products: M and K at most 64 (the channel counts),
+// N the pixels of a sample (long, contiguous in B and C: transB = 0).  As a
+// tiled GEMM the M x K operand half-fills a 64 x 64 tile and the epilogue's
+// streams dominate; here a thread owns two adjacent pixels, reads their K
+// values as BF16 pairs (coalesced across the block), and forms the M outputs
+// four at a time from op(A) in shared memory (FP32, exact copies of the BF16
+// weights: every product is exact, as on the tensor cores), the four rows'
+// epilogue inputs fetched together before their sums, so that their load
+// latencies overlap; stores are pairs.  Requires even N, leading dimensions
+// and batch strides, and 8-byte aligned FP32 / 4-byte aligned BF16 arrays.
+constexpr int PW_THREADS = 128;
+
+template <int MM, int KK>
+__global__ void __launch_bounds__(PW_THREADS) pointwise_kernel(const GemmArgs g)
+{
+    static_assert(MM % 4 == 0 && KK % 4 == 0, "rows in groups of 4, k in float4 reads");
+    __shared__ __align__(16) float As[MM][KK];
+    const int z = blockIdx.y;
+    const int z1 = z / g.nb2, z2 = z - z1 * g.nb2;
+    const bf16 *A = g.A + z1 * g.sA1 + z2 * g.sA2;
+    const bf16 *B = g.B + z1 * g.sB1 + z2 * g.sB2;
+    const long long cofs = z1 * g.sC1 + z2 * g.sC2;
+    for (int e = threadIdx.x; e < MM * KK; e += PW_THREADS) {
+        const int m = e / KK, k = e - m * KK;
+        As[m][k] = __bfloat162float(g.transA ? A[(long long)k * g.lda + m] : A[(long long)m * g.lda + k]);
+    }
+    __syncthreads();
+    const long long n = ((long long)blockIdx.x * PW_THREADS + threadIdx.x) * 2;
+    if (n >= g.N) return;
+    float b0[KK], b1[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(B + (long long)k * g.ldb + n);
+        b0[k] = __low2float(v);
+        b1[k] = __high2float(v);
+    }
+#pragma unroll 1
+    for (int m0 = 0; m0 < MM; m0 += 4) {
+        float2 ad[4], ax[4], cf[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long off = cofs + (long long)(m0 + u) * g.ldc + n;
+            ad[u] = g.add ? *reinterpret_cast<const float2 *>(g.add + off) : make_float2(0.f, 0.f);
+            ax[u] = g.act == ACT_GELU_GRAD ? *reinterpret_cast<const float2 *>(g.aux + off) : make_float2(0.f, 0.f);
+            cf[u] = g.beta != 0.f ? *reinterpret_cast<const float2 *>(g.Cf + off) : make_float2(0.f, 0.f);
+        }
+        const float2 bn = g.bias_n ? *reinterpret_cast<const float2 *>(g.bias_n + n) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = m0 + u;
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < KK; k += 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(&As[m][k]);
+                a0 = fmaf(a.x, b0[k], a0);
+                a1 = fmaf(a.x, b1[k], a1);
+                a0 = fmaf(a.y, b0[k + 1], a0);
+                a1 = fmaf(a.y, b1[k + 1], a1);
+                a0 = fmaf(a.z, b0[k + 2], a0);
+                a1 = fmaf(a.z, b1[k + 2], a1);
+                a0 = fmaf(a.w, b0[k + 3], a0);
+                a1 = fmaf(a.w, b1[k + 3], a1);
+            }
+            const long long off = cofs + (long long)m * g.ldc + n;
+            float v0 = g.alpha * a0, v1 = g.alpha * a1;
+            if (g.beta != 0.f) v0 += g.beta * cf[u].x, v1 += g.beta * cf[u].y;
+            if (g.bias_m) v0 += g.bias_m[m], v1 += g.bias_m[m];
+            if (g.bias_n) v0 += bn.x, v1 += bn.y;
+            if (g.add) v0 += ad[u].x, v1 += ad[u].y;
+            if (g.pre) *reinterpret_cast<float2 *>(g.pre + off) = make_float2(v0, v1);
+            if (g.act == ACT_GELU) {
+                v0 = gelu_f(v0);
+                v1 = gelu_f(v1);
+            } else if (g.act == ACT_GELU_GRAD) {
+                v0 *= gelu_grad_f(ax[u].x);
+                v1 *= gelu_grad_f(ax[u].y);
+            }
+            if (g.Cf) *reinterpret_cast<float2 *>(g.Cf + off) = make_float2(v0, v1);
+            if (g.Cb) *reinterpret_cast<__nv_bfloat162 *>(g.Cb + off) = __floats2bfloat162_rn(v0, v1);
+        }
+    }
+}
+
+template <int MM, int KK>
+inline bool pointwise_try(const GemmArgs &g, cudaStream_t s, cudaError_t &e)
+{
+    if (g.M != MM || g.K != KK) return false;
+    const dim3 grid((unsigned)((g.N / 2 + PW_THREADS - 1) / PW_THREADS), g.batch, 1);
+    pointwise_kernel<MM, KK><<<grid, PW_THREADS, 0, s>>>(g);
+    e = cudaGetLastError();
+    return true;
+}
+
+// The pointwise kernel's layout conditions (see above).
+inline bool pointwise_fits(const GemmArgs &g)
+{
+    auto al = [](const void *p, unsigned a) { return ((uintptr_t)p % a) == 0; };
+    const bool even = g.N % 2 == 0 && g.ldb % 2 == 0 && g.ldc % 2 == 0 && g.sB1 % 2 == 0 && g.sB2 % 2 == 0 &&
+                      g.sC1 % 2 == 0 && g.sC2 % 2 == 0;
+    return g.transB == 0 && g.N >= 1024 && g.batch <= 65535 && even && al(g.B, 4) && al(g.Cb, 4) && al(g.Cf, 8) &&
+           al(g.add, 8) && al(g.pre, 8) && al(g.aux, 8) && al(g.bias_n, 8);
+}
+
 inline cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
 {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+    if (pointwise_fits(g)) {
+        cudaError_t e = cudaSuccess;
+        if (pointwise_try<32, 32>(g, s, e) || pointwise_try<64, 32>(g, s, e) || pointwise_try<32, 64>(g, s, e))
+            return e;
+    }
     const dim3 grid((g.M + GBM - 1) / GBM, (g.N + GBN - 1) / GBN, g.batch);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
     gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
