@@ -52,12 +52,13 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
 def csrc_sha() -> str:
-    """sha256 (16 hex) of the CUDA/C++ sources the kernels are built from."""
+    """sha256 (16 hex) of the CUDA/C++ sources the heat kernels are built from
+    (the heat_* files: the surrogate's sources do not change them)."""
     import hashlib
     d = os.path.join(ROOT, "paper_1912_03744_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if f.startswith("heat_") and f.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(f.encode())
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
