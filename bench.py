@@ -168,6 +168,32 @@ def _reduce_max(x, ws):
     return float(t.item())
 
 
+def _reduce_sum(x, ws):
+    """The sum of x over the ranks."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_members(cells, ws):
+    """Members of an ensemble dealt to ws ranks with balanced cell counts:
+    largest first, each to the rank with the fewest cells so far (ties to the
+    lowest rank); deterministic, every member on exactly one rank, each
+    rank's list in ascending member order."""
+    load = [0] * ws
+    out = [[] for _ in range(ws)]
+    for i in sorted(range(len(cells)), key=lambda i: (-cells[i], i)):
+        r = min(range(ws), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += cells[i]
+    return [sorted(o) for o in out]
+
+
 def _whole_job(units_per_rank, ws, max_seconds):
     """Whole-job throughput of ws replicas that each processed units_per_rank
     units, over the slowest rank's time (weak scaling)."""
@@ -327,14 +353,21 @@ def step_roofline(cells_active, word, ms_per_step):
             "frac": ach / peak, "traffic": None, "algorithmic_bytes": b, "peak_kind": kind, "cells": "active"}
 
 
-def time_ensemble(steps, warmup, precision="fp32", tuning=None):
+def time_ensemble(steps, warmup, precision="fp32", tuning=None, rank=0, ws=1):
     """The 512-member batched ensemble (Nr 64..512, Nz 128..1024, jittered
     layers and materials), dt = 50 x each member's explicit limit, autotuned
     schedule, graph-replayed steps; CUDA events on the caller's stream around
-    all timed steps.  The two field buffers (~0.7 GB in FP32) exceed L2."""
+    all timed steps.  The two field buffers (~0.7 GB in FP32) exceed L2.
+    With ws ranks the members are sharded over them by cell count
+    (shard_members: the ensemble's members are independent problems, so no
+    data crosses ranks); the time is the slowest rank's, the work all
+    ranks' (strong scaling of the fixed ensemble)."""
     import torch
     from paper_1912_03744_gb300 import HeatBatch
     probs = H.config3_members(512)
+    n_all = len(probs)
+    if ws > 1:
+        probs = [probs[i] for i in shard_members([q.Nr * q.Nz for q in probs], ws)[rank]]
     t0 = time.perf_counter()
     b = HeatBatch(probs, [1.0] * len(probs), precision=precision)
     b.set_dt([H.DT_FACTOR * m.tau_exp for m in b.members])
@@ -354,11 +387,18 @@ def time_ensemble(steps, warmup, precision="fp32", tuning=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ok = all(np.isfinite(b.members[i].field()).all() for i in (0, len(probs) // 2, len(probs) - 1))
+    cells = b.cells
+    if ws > 1:
+        ms = _reduce_max(ms, ws)
+        act = int(_reduce_sum(act, ws))
+        cells = int(_reduce_sum(cells, ws))
+        ok = _reduce_sum(0.0 if ok else 1.0, ws) == 0.0
     out = {"workload": "config3: 512-member ensemble, Nr U{64..512}, Nz U{128..1024}, seed 3, dt=50*tau_exp",
-           "precision": precision, "members": len(probs), "cells": b.cells, "active_cells": act,
+           "precision": precision, "members": n_all, "cells": cells, "active_cells": act,
+           "sharding": f"members over {ws} ranks by cell count" if ws > 1 else "one rank",
            "steps": steps, "ms_per_step": ms / steps, "cell_steps_per_s": act * steps / (ms * 1e-3),
-           "member_steps_per_s": len(probs) * steps / (ms * 1e-3),
-           "fields_per_s_500_steps": len(probs) / (500 * ms / steps * 1e-3),
+           "member_steps_per_s": n_all * steps / (ms * 1e-3),
+           "fields_per_s_500_steps": n_all / (500 * ms / steps * 1e-3),
            "tuning": dict(zip(("rK", "band", "zwpb"), b.tuning())), "tune_ms_per_step": tune_ms,
            "launches_per_step": b.launches_per_step(), "graph_replay": True, "create_s": create_s,
            "finite": bool(ok), "l2": "inputs larger than L2",
@@ -616,7 +656,8 @@ def main():
     e2e_s, e2e_bytes = time_e2e(p, args.precision, args.steps)
     c1 = time_config1()
     full = time_full_method()
-    ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning)
+    ens = None if args.no_ensemble else time_ensemble(args.ensemble_steps, args.warmup, tuning=ens_tuning,
+                                                      rank=rank, ws=ws)
     c4 = None if args.no_config4 else time_config4(args.config4_steps, args.warmup)
     surr = None if args.no_surrogate else time_surrogate(args.surrogate_train, args.surrogate_epochs)
     _barrier(ws)
