@@ -123,7 +123,11 @@ int heat_create(const heat_geometry *geom, const heat_materials *mat, const heat
 int heat_set_dt(heat_ctx *ctx, double dt);
 
 /* Enqueue n >= 0 ADI steps (eqs. "scheme_eq_1" then "scheme_eq_2" per step)
- * on the context stream.  Asynchronous; launch errors return HEAT_ERR_CUDA. */
+ * on the context stream.  Asynchronous; launch errors return HEAT_ERR_CUDA.
+ * An FP64 context whose lines are at most 256 cells long in both directions
+ * (with the default r-sweep rule) runs all n steps in one cooperative launch
+ * whose half steps are separated by a grid barrier with a bounded wait; a
+ * wait that runs out is reported by heat_sync as HEAT_ERR_TIMEOUT. */
 int heat_step(heat_ctx *ctx, int n);
 
 /* One half-step only: dir = 0 runs half-step 1 (eq. "scheme_eq_1": implicit
