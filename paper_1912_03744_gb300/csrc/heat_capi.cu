@@ -207,7 +207,7 @@ int upload_rline(heat_ctx *ctx)
     const Grid &g = ctx->g;
     for (int j = 0; j < g.Nz;) {
         int n = 1;
-        while (n < kRLineR && j + n < g.Nz && g.rowcls[j + n] == g.rowcls[j]) ++n;
+        while (n < rline_rows(ctx->precision == HEAT_FP64) && j + n < g.Nz && g.rowcls[j + n] == g.rowcls[j]) ++n;
         zcl.push_back(j | (n << 16));
         j += n;
     }

@@ -102,6 +102,10 @@ struct RLine {
 };
 // Rows a line team solves together (one unit).
 constexpr int kRLineR = 2;
+// rows a team of the line-team r-sweep solves together: 2 in FP32; 1 in FP64,
+// where the per-team buffer of forward results (8 bytes a cell) would
+// otherwise hold the SM to 6 resident warps of an FP64-bound kernel
+constexpr int rline_rows(bool fp64) { return fp64 ? 1 : kRLineR; }
 
 // theta_bc of the faces r_lo, r_hi, z_lo, z_hi
 struct BcVals {

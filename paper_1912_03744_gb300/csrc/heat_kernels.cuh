@@ -1339,7 +1339,7 @@ template <typename real, int MODE>
 static cudaError_t plan_rline(SweepArgs<real> *h, int n, Tuning &tu, Launch &L)
 {
     constexpr int K = rline_K<real>();
-    constexpr int R = kRLineR;
+    constexpr int R = rline_rows(sizeof(real) == 8);
     const void *fn = (const void *)rline_kernel<real, K, R, MODE>;
     int maxseg = 1;
     for (int m = 0; m < n; ++m) {
