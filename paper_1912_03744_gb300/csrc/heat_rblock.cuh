@@ -44,6 +44,7 @@ __device__ __forceinline__ void rb_cp4(void *smem, const void *gmem, int src_byt
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
 }
 __device__ __forceinline__ void rb_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p)); }
 template <int N>
 __device__ __forceinline__ void rb_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 __device__ __forceinline__ void rb_bar(int id, int nthreads)
@@ -94,8 +95,14 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     const int bar_id = 1 + slot;
 
     // this thread's K cells of row x into its ring slot (zero past the field)
+    // (rows past jstart + band, which no pass of the slot reads, commit an
+    // empty group)
     auto fetch = [&](int x) {
         real *dst = ring + (size_t)((x - jstart + 1) & (NRING - 1)) * Np;  // x >= jstart - 1
+        if (x > jstart + band) {
+            rb_commit();
+            return;
+        }
         const bool rin = x >= 0 && x < Nz;
         const real *src = th + (size_t)(rin ? x : 0) * Nr;
         if (vec) {
@@ -113,6 +120,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         }
         rb_commit();
     };
+    const int a0 = rowcls[min(jstart, Nz - 1)];  // class of the band's first row
     // column class of the thread's cells: one for all K, or per cell (a chunk
     // across a layer interface)
     // zc0: class of the first cell, zc1: of the last cell inside the field;
@@ -132,12 +140,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             if (c == zc1 && c != zc0) zsel |= 1u << k;
             zmany = zmany || (c != zc0 && c != zc1);
         }
-
-    const bool zany = __any_sync(FULL, zmany);
-    const bool zone = __all_sync(FULL, zsel == 0u && !zmany);  // one column class in every chunk of the warp
-    pdl_wait();
-    // prologue: rows jstart-1 .. jstart+NRING-2
-    for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
+    bool zany, zone;  // (set below) some cell of the warp has a third class; one column class in every chunk of the warp
 
     // class state: the coefficients scaled by the pivot, fx = xm inv (also
     // the Thomas multiplier f), cx = xp inv (also cp), qi = q inv, and inv
@@ -150,17 +153,27 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     // of warp v's backward map, prod of H over the warps between (0 for v <= wil)
     real jf = real(0), jh = real(0);
 
-    // load the coefficients of class a and the scan multipliers (all threads of the slot)
-    auto load_class = [&](int a) {
+    // the coefficients of class a as stored (issued together; used by class_finish)
+    auto class_loads = [&](int a) {
         const size_t ro = (size_t)a * Nr;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int i = i0 + k;
             const bool in = i < Nr;
             iv[k] = in ? R.inv[ro + i] : real(0);
-            fx[k] = in ? R.xm[ro + i] * iv[k] : real(0);
-            cx[k] = in ? R.xp[ro + i] * iv[k] : real(0);
-            qi[k] = in ? R.q[ro + i] * iv[k] : real(0);
+            fx[k] = in ? R.xm[ro + i] : real(0);
+            cx[k] = in ? R.xp[ro + i] : real(0);
+            qi[k] = in ? R.q[ro + i] : real(0);
+        }
+        acls = a;
+    };
+    // scale them by the pivot and form the scan multipliers (all threads of the slot)
+    auto class_finish = [&]() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            fx[k] *= iv[k];
+            cx[k] *= iv[k];
+            qi[k] *= iv[k];
         }
         Fc = Hc = real(1);
 #pragma unroll
@@ -192,7 +205,6 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
             if (lane == 31) sxF[slot][wil] = pf;
             if (lane == 0) sxH[slot][wil] = ph;
         }
-        acls = a;
     };
     // (wide lines, after the barrier that publishes sxF / sxH)
     auto join_multipliers = [&]() {
@@ -413,6 +425,34 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         for (int r = 0; r < NR; ++r) fetch(j + NRING - 1 + r);
     };
 
+    // Start of the band.  The tables do not change between launches, so the
+    // first class's coefficients, and the z coefficients of the band's rows
+    // (into L1), are requested before the wait for the previous kernel and
+    // ahead of the ring's rows, which would otherwise queue them behind
+    // several megabytes of row traffic.
+    class_loads(a0);
+    {
+        const int jl = min(jstart + band, Nz - 1);
+        for (int x = min(jstart, Nz - 1); x <= jl; x += 16) {
+            prefetch_l1(Z.xm + (size_t)zc0 * Nz + x);
+            prefetch_l1(Z.xp + (size_t)zc0 * Nz + x);
+            if (zc1 != zc0) {
+                prefetch_l1(Z.xm + (size_t)zc1 * Nz + x);
+                prefetch_l1(Z.xp + (size_t)zc1 * Nz + x);
+            }
+        }
+    }
+    zany = __any_sync(FULL, zmany);
+    zone = __all_sync(FULL, zsel == 0u && !zmany);
+    pdl_wait();
+    // prologue: rows jstart-1 .. jstart+NRING-2
+    for (int x = jstart - 1; x <= jstart + NRING - 2; ++x) fetch(x);
+    class_finish();
+    if (wide) {
+        rb_bar(bar_id, G);
+        join_multipliers();
+    }
+
     // The slots of a warp (sub-warp lines) walk their bands in lockstep, and
     // every decision below is taken for the whole warp, so the warp's
     // shuffles always see all 32 lanes; the warps of a wide line see the same
@@ -422,7 +462,8 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         const int a = rowcls[min(j, Nz - 1)];
         if (__any_sync(FULL, a != acls)) {
             if (wide) rb_bar(bar_id, G);  // nobody still reads the previous class's sxF / sxH
-            load_class(a);
+            class_loads(a);
+            class_finish();
             if (wide) {
                 rb_bar(bar_id, G);
                 join_multipliers();
