@@ -117,6 +117,8 @@ struct BcVals {
 // launch serves one problem or a whole batch.  The field ping-pongs between
 // f0 and f1: with flip = 0 a sweep reads f0 and writes f1, with flip = 1 the
 // reverse.
+constexpr int kMaxRun = 16;  // row-class runs kept in the sweep arguments
+
 template <typename real>
 struct SweepArgs {
     int Nr, Nz;
@@ -149,6 +151,13 @@ struct SweepArgs {
     int rw_K, rw_ncc;
     int rw_stall;             // failure-detection test: the walk's first wait runs out
     int *status;              // device status word: bit 0 = a bounded wait gave up
+    // row-class runs of the instance: run r is rows [run_lo[r], run_lo[r+1])
+    // of one row class (n_run = 0: more than kMaxRun runs).  The register-
+    // resident r-sweep of a single instance splits each run into bands of
+    // `band` rows, run r owning slots [run_slot[r], run_slot[r+1]); rb_runs = 0:
+    // uniform bands of the whole height
+    int n_run, rb_runs;
+    int run_lo[kMaxRun + 1], run_slot[kMaxRun + 1];
 };
 
 // One kernel launch of a sweep.  Every sweep kernel takes a device array of

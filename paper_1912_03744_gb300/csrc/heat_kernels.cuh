@@ -1435,6 +1435,38 @@ static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L
         }
         return mx;
     };
+    for (int m = 0; m < n; ++m) h[m].rb_runs = 0;
+    // A single instance whose lines take whole warps splits every row-class
+    // run into its own bands, so that no band changes class (a change costs
+    // the slot a class load and up to two one-row passes, and the slowest
+    // slot sets the launch's time): the smallest even band whose bands fit
+    // in one wave of slots.
+    if (n == 1 && h[0].G >= 32 && h[0].n_run > 0) {
+        SweepArgs<float> &a = h[0];
+        const int lpb = block / a.G;
+        const long long avail = (long long)kSMs * per_sm * lpb;
+        auto slots_for = [&](int b) {
+            long long t = 0;
+            for (int r = 0; r < a.n_run; ++r) t += (a.run_lo[r + 1] - a.run_lo[r] + b - 1) / b;
+            return t;
+        };
+        int b = tu.band > 0 ? tu.band : 2;
+        if (tu.band <= 0)
+            while (slots_for(b) > avail) b += 2;
+        a.band = b;
+        a.run_slot[0] = 0;
+        for (int r = 0; r < a.n_run; ++r)
+            a.run_slot[r + 1] = a.run_slot[r] + (a.run_lo[r + 1] - a.run_lo[r] + b - 1) / b;
+        a.rb_runs = 1;
+        tu.band = b;
+        tu.rK = 2;
+        L.fn = fn;
+        L.grid = dim3((a.run_slot[a.n_run] + lpb - 1) / lpb, 1, 1);
+        L.block = dim3(block, 1, 1);
+        L.smem = smem;
+        L.flip = true;
+        return cudaSuccess;
+    }
     int band = tu.band;
     if (band <= 0) {
         if (n == 1) {

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     const SweepArgs<real> &A = args[blockIdx.y];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;
-    const int Nr = A.Nr, Nz = A.Nz, G = A.G, band = A.band;
+    const int Nr = A.Nr, Nz = A.Nz, G = A.G;
     const int tid = threadIdx.x;
     const int lpb = blockDim.x / G;
     const int slot = tid / G, g = tid % G;
@@ -74,9 +74,22 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     const int wil = g >> 5;  // warp index within a wide line
     const int nwl = G >> 5;  // warps per wide line
     const bool wide = G > 32;
-    const int jstart = (blockIdx.x * lpb + slot) * band;
+    // the slot's band: rows [jstart, jstart + band) (stored below Nz); with
+    // row-class runs (lines of whole warps, so a warp holds one slot) the
+    // bands of run r start at run_lo[r]
+    const int sid = blockIdx.x * lpb + slot;
+    int jstart, band = A.band;
     pdl_launch_dependents();
-    if ((int)blockIdx.x * lpb * band >= Nz) return;  // past this instance (block-uniform)
+    if (A.rb_runs) {
+        if (sid >= A.run_slot[A.n_run]) return;  // a slot past the last band (warp-uniform)
+        int r = 0;
+        while (r + 1 < A.n_run && sid >= A.run_slot[r + 1]) ++r;
+        jstart = A.run_lo[r] + (sid - A.run_slot[r]) * band;
+        band = min(band, A.run_lo[r + 1] - jstart);
+    } else {
+        jstart = sid * band;
+        if ((int)blockIdx.x * lpb * band >= Nz) return;  // past this instance (block-uniform)
+    }
     const int jend = min(Nz, jstart + band);  // rows this slot stores: [jstart, jend)
     const int i0 = g * K;
     const bool vec = EXACT || (Nr & 3) == 0;

@@ -50,6 +50,17 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
     a.nch = ctx->zp.n_chunks;
     a.rowcls = ctx->d_rowcls;
     a.colcls = ctx->d_colcls;
+    a.n_run = 0;
+    a.rb_runs = 0;
+    for (int j = 0; j < a.Nz && a.n_run <= kMaxRun; ++j)
+        if (j == 0 || ctx->g.rowcls[j] != ctx->g.rowcls[j - 1]) {
+            if (a.n_run < kMaxRun) a.run_lo[a.n_run] = j;
+            ++a.n_run;
+        }
+    if (a.n_run > kMaxRun)
+        a.n_run = 0;
+    else
+        a.run_lo[a.n_run] = a.Nz;
     a.R64 = ctx->dR.full;
     a.Z64 = ctx->dZ.full;
     a.R2 = ctx->dR.t2;
