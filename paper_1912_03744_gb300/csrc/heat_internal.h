@@ -157,7 +157,7 @@ struct SweepArgs {
     // `band` rows, run r owning slots [run_slot[r], run_slot[r+1]); rb_runs = 0:
     // uniform bands of the whole height
     int n_run, rb_runs;
-    int run_lo[kMaxRun + 1], run_slot[kMaxRun + 1];
+    int run_lo[kMaxRun + 1], run_slot[kMaxRun + 1], run_cls[kMaxRun];
 };
 
 // One kernel launch of a sweep.  Every sweep kernel takes a device array of
@@ -169,6 +169,10 @@ struct Launch {
     bool flip = false;
     int cluster = 1;  // blocks per thread-block cluster along x (1: no cluster)
     bool pdl = true;  // launched with programmatic stream serialization
+    // kernels that also take the first instance's arguments by value (a
+    // __grid_constant__ parameter: read from the constant bank, so a band's
+    // first loads do not wait for a fetch of the arguments): their bytes
+    std::vector<unsigned char> pargs;
 };
 
 // Launch schedule of both half-steps for one set of instances (one problem,

@@ -1415,8 +1415,11 @@ static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L
         h[m].G = G;
         exact = exact && G * K == h[m].Nr && h[m].Nr % 4 == 0;
     }
-    const void *fn = exact ? (const void *)rblock_kernel<K, kRBlockRing, true>
-                           : (const void *)rblock_kernel<K, kRBlockRing, false>;
+    // a single instance reads its arguments from the by-value copy
+    const void *fn = n == 1 ? (exact ? (const void *)rblock_kernel<K, kRBlockRing, true, true>
+                                     : (const void *)rblock_kernel<K, kRBlockRing, false, true>)
+                            : (exact ? (const void *)rblock_kernel<K, kRBlockRing, true, false>
+                                     : (const void *)rblock_kernel<K, kRBlockRing, false, false>);
     const int block = 256;
     const size_t smem = (size_t)kRBlockRing * block * K * sizeof(float);
     cudaError_t e = allow_smem(fn, smem);
@@ -1460,6 +1463,7 @@ static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L
         a.rb_runs = 1;
         tu.band = b;
         tu.rK = 2;
+        L.pargs.assign(1, 0);  // (the three-parameter kernel; filled at the end of the plan)
         L.fn = fn;
         L.grid = dim3((a.run_slot[a.n_run] + lpb - 1) / lpb, 1, 1);
         L.block = dim3(block, 1, 1);
@@ -1493,6 +1497,7 @@ static cudaError_t plan_rblock(SweepArgs<float> *h, int n, Tuning &tu, Launch &L
     L.block = dim3(block, 1, 1);
     L.smem = smem;
     L.flip = true;
+    L.pargs.assign(1, 0);
     return cudaSuccess;
 }
 
@@ -1786,6 +1791,12 @@ static cudaError_t plan_mode(SweepArgs<real> *h, int n, const Tuning &req, Sweep
     } else {
         if ((e = plan_zpass<real, MODE>(h, n, tu, plan.dir[1])) != cudaSuccess) return e;
     }
+    // by-value arguments: the first instance's final arguments
+    for (auto &dir : plan.dir)
+        for (Launch &L : dir)
+            if (!L.pargs.empty())
+                L.pargs.assign(reinterpret_cast<const unsigned char *>(&h[0]),
+                               reinterpret_cast<const unsigned char *>(&h[0]) + sizeof(SweepArgs<real>));
     plan.used = tu;
     return cudaSuccess;
 }

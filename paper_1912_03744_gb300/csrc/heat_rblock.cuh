@@ -58,11 +58,14 @@ struct RbRows {
     static constexpr int value = N;
 };
 
-template <int K, int NRING, bool EXACT>
-__global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *__restrict__ args, int flip)
+// BYVAL: one instance, whose arguments are read from the by-value parameter a1
+// (the constant bank) rather than from args in global memory.
+template <int K, int NRING, bool EXACT, bool BYVAL>
+__global__ void __launch_bounds__(256, 2)
+    rblock_kernel(const SweepArgs<float> *__restrict__ args, int flip, const __grid_constant__ SweepArgs<float> a1)
 {
     using real = float;
-    const SweepArgs<real> &A = args[blockIdx.y];
+    const SweepArgs<real> &A = BYVAL ? a1 : args[blockIdx.y];
     const real *__restrict__ th = flip ? A.f1 : A.f0;
     real *__restrict__ out = flip ? A.f0 : A.f1;
     const int Nr = A.Nr, Nz = A.Nz, G = A.G;
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
     // row-class runs (lines of whole warps, so a warp holds one slot) the
     // bands of run r start at run_lo[r]
     const int sid = blockIdx.x * lpb + slot;
-    int jstart, band = A.band;
+    int jstart, band = A.band, a0;  // a0: row class of the band's first row
     pdl_launch_dependents();
     if (A.rb_runs) {
         if (sid >= A.run_slot[A.n_run]) return;  // a slot past the last band (warp-uniform)
@@ -86,9 +89,11 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         while (r + 1 < A.n_run && sid >= A.run_slot[r + 1]) ++r;
         jstart = A.run_lo[r] + (sid - A.run_slot[r]) * band;
         band = min(band, A.run_lo[r + 1] - jstart);
+        a0 = A.run_cls[r];
     } else {
         jstart = sid * band;
         if ((int)blockIdx.x * lpb * band >= Nz) return;  // past this instance (block-uniform)
+        a0 = A.rowcls[min(jstart, Nz - 1)];
     }
     const int jend = min(Nz, jstart + band);  // rows this slot stores: [jstart, jend)
     const int i0 = g * K;
@@ -133,7 +138,6 @@ __global__ void __launch_bounds__(256, 2) rblock_kernel(const SweepArgs<float> *
         }
         rb_commit();
     };
-    const int a0 = rowcls[min(jstart, Nz - 1)];  // class of the band's first row
     // column class of the thread's cells: one for all K, or per cell (a chunk
     // across a layer interface)
     // zc0: class of the first cell, zc1: of the last cell inside the field;

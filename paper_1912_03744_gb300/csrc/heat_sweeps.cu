@@ -61,6 +61,7 @@ static void fill_args_t(const heat_ctx *ctx, void *dst)
         a.n_run = 0;
     else
         a.run_lo[a.n_run] = a.Nz;
+    for (int r = 0; r < a.n_run; ++r) a.run_cls[r] = ctx->g.rowcls[a.run_lo[r]];
     a.R64 = ctx->dR.full;
     a.Z64 = ctx->dZ.full;
     a.R2 = ctx->dR.t2;
@@ -127,7 +128,7 @@ cudaError_t make_plan(int precision, void *h, int n, const Tuning &req, SweepPla
 cudaError_t run_plan(const SweepPlan &plan, int dir, const void *d_args, int flip, cudaStream_t s)
 {
     for (const Launch &L : plan.dir[dir]) {
-        void *kargs[2] = {(void *)&d_args, (void *)&flip};
+        void *kargs[3] = {(void *)&d_args, (void *)&flip, (void *)L.pargs.data()};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = L.grid;
         cfg.blockDim = L.block;
