@@ -1011,7 +1011,6 @@ template <typename real, int SEG>
 __global__ void __launch_bounds__(32 * SEG) zcarry2_kernel(const SweepArgs<real> *__restrict__ args)
 {
     pdl_launch_dependents();
-    pdl_wait();
     const SweepArgs<real> &A = args[blockIdx.y];
     const int Nr = A.Nr, nch = A.nch;
     if ((int)blockIdx.x * 32 >= Nr) return;  // past this instance (block-uniform)
@@ -1026,15 +1025,23 @@ __global__ void __launch_bounds__(32 * SEG) zcarry2_kernel(const SweepArgs<real>
     const int c0 = sgm * m;
     const size_t st = (size_t)2 * Nr;
     real Bv[ZMAXM], Gv[ZMAXM], Fv[ZMAXM], Hv[ZMAXM], GPv[ZMAXM];
+    // the chunk constants do not change between launches: requested before
+    // the wait for the summary pass, whose results (zs) are read after it
+#pragma unroll
+    for (int u = 0; u < ZMAXM; ++u) {
+        const int c = c0 + u;
+        const bool ok = col && u < m && c < nch;
+        Fv[u] = ok ? chb[c * 4] : real(1);
+        Hv[u] = ok ? chb[c * 4 + 1] : real(1);
+        if constexpr (sizeof(real) == 4) GPv[u] = ok ? chb[c * 4 + 2] : real(0);  // (FP64: no registers left)
+    }
+    pdl_wait();
 #pragma unroll
     for (int u = 0; u < ZMAXM; ++u) {
         const int c = c0 + u;
         const bool ok = col && u < m && c < nch;
         Bv[u] = ok ? zs[c * st + i] : real(0);
         Gv[u] = ok ? zs[c * st + Nr + i] : real(0);
-        Fv[u] = ok ? chb[c * 4] : real(1);
-        Hv[u] = ok ? chb[c * 4 + 1] : real(1);
-        if constexpr (sizeof(real) == 4) GPv[u] = ok ? chb[c * 4 + 2] : real(0);  // (FP64: no registers left)
     }
     // forward: D_c = B_c + F_c D_{c-1}
     real F = real(1), B = real(0);
