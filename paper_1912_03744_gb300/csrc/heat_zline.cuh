@@ -445,19 +445,27 @@ struct ZWalk {
     }
     // Walk rows [j0, j1) calling emit(j, d, e) with the right-hand side d of
     // row j and its table values e (E = 1: shared by the lane's columns).
+    // A chunk of several row classes (ucls < 0) reads the classes of 32 rows
+    // at a time, one per lane, and takes row j's by a shuffle: no row waits
+    // for a load of its class.
     template <int E, typename Emit>
     __device__ __forceinline__ void walk(int ucls, const LineTab<real> &R, Emit emit)
     {
         row(th, j0 - 1, tm);
         row(th, j0, t);
         if (ucls >= 0) row_class(ucls, R);
+        int rcl = ucls < 0 ? rowcls[min(j0 + lane, Nz - 1)] : 0;
         Group A, B;
         auto proc = [&](int x, const Group &G) {
 #pragma unroll
             for (int p = 0; p < ZQ; ++p) {
                 const int j = x + p;
                 if (j < j1) {
-                    if (ucls < 0) row_class(rowcls[j], R);
+                    if (ucls < 0) {
+                        const int jj = j - j0;
+                        if (jj > 0 && (jj & 31) == 0) rcl = rowcls[min(j + lane, Nz - 1)];
+                        row_class(__shfl_sync(HEAT_FULL_MASK, rcl, jj & 31), R);
+                    }
                     real e[E][8], d[V];
                     tab<E>(j, e);
                     rhs<E>(G, p, e, d);
