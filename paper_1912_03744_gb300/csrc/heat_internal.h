@@ -112,13 +112,13 @@ struct BcVals {
     double th[4];
 };
 
+constexpr int kMaxRun = 16;  // row-class runs kept in the sweep arguments
+
 // Everything a sweep kernel needs about one problem instance.  Kernels take
 // a device array of these and pick their instance from a grid index, so one
 // launch serves one problem or a whole batch.  The field ping-pongs between
 // f0 and f1: with flip = 0 a sweep reads f0 and writes f1, with flip = 1 the
 // reverse.
-constexpr int kMaxRun = 16;  // row-class runs kept in the sweep arguments
-
 template <typename real>
 struct SweepArgs {
     int Nr, Nz;
@@ -169,9 +169,11 @@ struct Launch {
     bool flip = false;
     int cluster = 1;  // blocks per thread-block cluster along x (1: no cluster)
     bool pdl = true;  // launched with programmatic stream serialization
-    // kernels that also take the first instance's arguments by value (a
-    // __grid_constant__ parameter: read from the constant bank, so a band's
-    // first loads do not wait for a fetch of the arguments): their bytes
+    // kernels with a third parameter, the first instance's arguments by value
+    // (__grid_constant__: read from the constant bank, so a band's first
+    // loads do not wait for a fetch of the arguments).  A plan builder marks
+    // such a launch with a non-empty pargs; plan_mode then stores in it the
+    // bytes of the first instance's final arguments, which run_plan passes
     std::vector<unsigned char> pargs;
 };
 
